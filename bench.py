@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the D2Q37 thermal LB step on GB300 (one JSON line on rank 0).
+
+Workload (default): a 2048 x 4096 Rayleigh-Taylor lattice (8,388,608 sites,
+32 seeded interface modes, tau = 0.6, g = 1e-5, walls at T = 0.5 / 1.5),
+float64 populations (two copies, 2 x 2.49 GB, far larger than L2).  One
+"step" is one fused propagate + bc + collide launch over the whole lattice.
+
+value        float64 MLUPS (million lattice-site updates per second), state
+             resident in HBM, CUDA-event time over K steps.
+fp32_store   the same lattice stored as float32 deviations f_l - w_l rho0.
+adjoint      one adjoint step (recompute + transposed collide + push) over
+             the same lattice, as a ratio to the forward step time.
+e2e          the same metric through the C ABI with pinned HOST buffers:
+             per step set_state(host) -> step -> get_state(host).
+roofline     the fused float64 kernel against the FP64 FMA rate measured by
+             the library's probe (the step is FP64-pipe bound).
+cpu_baseline the float64 oracle (NumPy) on a bounded sample of the workload.
+
+--impl reference times the oracle itself (the only reference this method
+has) on the host cores, with the same metric and workload.
+Under torchrun each rank steps its own replica lattice (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q37 MLUPS, FP64 vs FP32-store, and adjoint/forward step time ratio, 1 GB300"
+WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-5"
+
+# Algorithmic float64 work of the fused step per site (counted from the
+# kernel's formulation; see the design notes): instructions and flops
+# (an FMA counts 2 flops).
+FP64_INSTR_PER_SITE = 377
+FP64_FLOP_PER_SITE = 547
+BYTES_PER_SITE_FP64 = 2 * 37 * 8
+BYTES_PER_SITE_FP32 = 2 * 37 * 4
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lx", type=int, default=2048)
+    ap.add_argument("--ly", type=int, default=4096)
+    ap.add_argument("--only", default="", help="comma list of sections: fp64,fp32,adjoint,e2e,cpu")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def rt_lattice(lx, ly, precision, rho0=None):
+    import synth
+    from paper_1703_00186_gb300.lbm import Lattice
+    rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 32, 0)
+    r0 = float(rho.mean()) if rho0 is None else rho0
+    lat = Lattice(lx, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb, precision=precision, rho0=r0)
+    lat.init(rho, ux, uy, T)
+    return lat, (rho, ux, uy, T)
+
+
+def time_steps(lat, k, torch):
+    """CUDA-event time (ms) of k fused steps on the lattice's stream."""
+    s = lat.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    lat.step(k)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def dist_max(v, torch, world):
+    if world <= 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(torch, world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def cpu_baseline(lx, ly, budget_s):
+    """Time the float64 oracle on a column slab of the workload."""
+    import numpy as np
+
+    import synth
+    from oracle import model as M
+    rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 32, 0)
+    width = 32
+    p_probe = M.Params(width, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
+    f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
+    t0 = time.perf_counter()
+    M.step(f, p_probe)
+    per_site = (time.perf_counter() - t0) / (width * ly)
+    # grow the slab so that the sample takes about budget_s
+    width = int(max(32, min(lx, budget_s / max(per_site, 1e-9) / ly / 2)))
+    p = M.Params(width, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
+    f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
+    steps = 2
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = M.step(f, p)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(M.physical(f)).all()
+    return {"value": width * ly * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{width}x{ly} column slab of the 2048x4096 RT lattice (periodic in x), "
+                      f"{steps} steps, NumPy float64, single thread; {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(args.lx, args.ly, max(2.0, args.cpu_seconds / 3))
+    # each reference "step" is a bounded oracle sample of the same workload
+    import numpy as np
+
+    import synth
+    from oracle import model as M
+    rho, ux, uy, T, tt, tb = synth.rt_fields(args.lx, args.ly, 32, 0)
+    width = 32
+    p = M.Params(width, args.ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
+    f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
+    for _ in range(min(args.warmup, 3)):
+        f = M.step(f, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = M.step(f, p)
+    dt = time.perf_counter() - t0
+    v = width * args.ly * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "lx": args.lx, "ly": args.ly,
+                                            "sample_columns": width},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{width}x{args.ly} column slab per step, NumPy float64, single thread"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline_calibration": cb}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1703_00186_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(torch, world)
+    import ctypes
+
+    from paper_1703_00186_gb300 import _lib as L
+    lib = L.load()
+    only = set(filter(None, args.only.split(","))) or {"fp64", "fp32", "adjoint", "e2e", "cpu"}
+    lx, ly, K, W = args.lx, args.ly, args.steps, args.warmup
+    sites = lx * ly
+    out = {}
+
+    # float64 peak of this GPU (FMA probe)
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    rc = lib.lbm_probe_fma(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 4096, 0,
+                           ctypes.byref(tf), ctypes.byref(ms))
+    fp64_peak = tf.value if rc == 0 else None
+
+    clocks = None
+    if "fp64" in only:
+        lat, _ = rt_lattice(lx, ly, "fp64")
+        lat.step(W)
+        sampler = ClockSampler(local)
+        sampler.start()
+        barrier(torch, world)
+        t_ms = time_steps(lat, K, torch)
+        barrier(torch, world)
+        clocks = sampler.stop()
+        t_ms = dist_max(t_ms, torch, world)
+        finite = lat.check_finite()
+        out["fp64"] = {"ms": t_ms, "mlups": world * sites * K / (t_ms * 1e-3) / 1e6, "finite": finite}
+        del lat
+        torch.cuda.empty_cache()
+    if "fp32" in only:
+        lat, _ = rt_lattice(lx, ly, "fp32")
+        lat.step(W)
+        barrier(torch, world)
+        t_ms = dist_max(time_steps(lat, K, torch), torch, world)
+        out["fp32"] = {"ms": t_ms, "mlups": world * sites * K / (t_ms * 1e-3) / 1e6,
+                       "finite": lat.check_finite()}
+        del lat
+        torch.cuda.empty_cache()
+    if "adjoint" in only:
+        lat, _ = rt_lattice(lx, ly, "fp64")
+        lat.step(W)
+        f_t = lat.state().clone()
+        lam_a = lat.new_cotangent(0.0).normal_()
+        lam_b = lat.new_cotangent(0.0)
+        ka = max(3, K // 4)
+        for _ in range(2):
+            lat.adjoint_step(f_t, lam_a, lam_b)
+        s = lat.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for i in range(ka):
+            if i % 2 == 0:
+                lat.adjoint_step(f_t, lam_a, lam_b)
+            else:
+                lat.adjoint_step(f_t, lam_b, lam_a)
+        e1.record(s)
+        e1.synchronize()
+        ta = dist_max(e0.elapsed_time(e1) / ka, torch, world)
+        tf_ms = dist_max(time_steps(lat, ka, torch) / ka, torch, world)
+        out["adjoint"] = {"adjoint_ms_per_step": ta, "forward_ms_per_step": tf_ms, "ratio": ta / tf_ms}
+        del lat, f_t, lam_a, lam_b
+        torch.cuda.empty_cache()
+    if "e2e" in only:
+        lat, _ = rt_lattice(lx, ly, "fp64")
+        host_in = torch.empty(lat.shape, dtype=lat.dtype, pin_memory=True)
+        host_out = torch.empty(lat.shape, dtype=lat.dtype, pin_memory=True)
+        lat.get_state(host_in)
+        torch.cuda.synchronize()
+        ke = max(3, min(K, 20))
+        for _ in range(2):
+            lat.set_state(host_in).step(1).get_state(host_out)
+        barrier(torch, world)
+        s = lat.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(ke):
+            lat.set_state(host_in).step(1).get_state(host_out)
+        e1.record(s)
+        e1.synchronize()
+        te = dist_max(e0.elapsed_time(e1), torch, world)
+        out["e2e"] = {"value": world * sites * ke / (te * 1e-3) / 1e6, "unit": "MLUPS",
+                      "h2d_bytes_per_step": lat.nbytes, "d2h_bytes_per_step": lat.nbytes,
+                      "steps": ke, "path": "lbm_set_state(pinned host) + lbm_step(1) + lbm_get_state(pinned host)"}
+        del lat, host_in, host_out
+    barrier(torch, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    res = {"metric": METRIC, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "lx": lx, "ly": ly, "sites": sites, "tau": 0.6, "g": 1e-5,
+                      "modes": 32, "seed": 0, "t_top": 0.5, "t_bottom": 1.5,
+                      "l2": "inputs larger than L2 (state 2 x %.2f GB)" % (37 * (ly + 6) * lx * 8 / 1e9),
+                      "parallelism": f"replicas x{world}"}}
+    if "fp64" in out:
+        f64 = out["fp64"]
+        t_launch = f64["ms"] / K * 1e-3
+        res["value"] = f64["mlups"]
+        res["ms_per_step"] = f64["ms"] / K
+        res["gpu_launches"] = K
+        res["finite_after_timed_steps"] = f64["finite"]
+        peak = fp64_peak if fp64_peak else FP64_NOMINAL_TFLOPS
+        achieved = FP64_FLOP_PER_SITE * sites / t_launch / 1e12
+        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": None,
+                           "peak_source": "measured FP64 FMA probe" if fp64_peak else "nominal 1.25 TF",
+                           "flop_per_site": FP64_FLOP_PER_SITE, "fp64_instr_per_site": FP64_INSTR_PER_SITE,
+                           "hbm_gbs": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9}
+        res["clocks"] = clocks
+    if "fp32" in out:
+        f32 = out["fp32"]
+        t_launch = f32["ms"] / K * 1e-3
+        res["fp32_store"] = {"mlups": f32["mlups"], "ms_per_step": f32["ms"] / K,
+                             "speedup_vs_fp64": (f32["mlups"] / out["fp64"]["mlups"]) if "fp64" in out else None,
+                             "hbm_gbs": BYTES_PER_SITE_FP32 * sites / t_launch / 1e9,
+                             "finite_after_timed_steps": f32["finite"]}
+    if "adjoint" in out:
+        res["adjoint"] = out["adjoint"]
+    if "e2e" in out:
+        res["e2e"] = out["e2e"]
+    res["fp64_probe_tflops"] = fp64_peak
+    if "cpu" in only:
+        res["cpu_baseline"] = cpu_baseline(lx, ly, args.cpu_seconds)
+    print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * lbm.h - C ABI of the GB300 D2Q37 thermal lattice Boltzmann library (liblbm.so).
+ *
+ * The library runs the time step of the D2Q37 thermal LB model of
+ * Calore et al., "Performance and portability of accelerated lattice
+ * Boltzmann applications with OpenACC" (arXiv 1703.00186):
+ *   eq. (1)  f_l(x, t+1) = f_l(x - c_l, t) - (1/tau) (f_l(x - c_l, t) - f_l^eq),
+ *   eq. (2)  rho = sum_l f_l,  rho u = sum_l c_l f_l,  D rho T = sum_l |c_l - u|^2 f_l,
+ * executed as propagate, then bc, then collide (Sect. 2), fused into one
+ * CUDA kernel per step for sm_103a.
+ *
+ * Model readings where the paper is silent (also in the design notes):
+ *  - Velocity set: the 37 integer vectors xi with |xi_x|,|xi_y| <= 3 and
+ *    |xi|^2 in {0,1,2,4,5,8,9,10}; c_l = r xi_l, with r and the shell weights
+ *    solved from the order-8 Gaussian isotropy conditions.
+ *  - Equilibrium: 4th-order Hermite expansion of the Maxwellian about T = 1.
+ *  - Collide: plain BGK, omega = 1/tau; gravity g along -y as the equilibrium
+ *    shift u' = u + tau g, T' = T + tau (1 - tau) g^2 / 2.
+ *  - Walls (bc, Sect. 2): top and bottom rows; after propagate, the 26 slots
+ *    per column and wall whose pull source lies beyond the wall are set to
+ *    M(x) q_l, where M(x) is the mass that crossed that wall and lands in
+ *    column x (summed in the order: population l ascending, then source row
+ *    ascending, round-to-nearest, no contraction) and q_l = phi_l / sum phi
+ *    over the 26 slots, phi_l = f^eq_l(1, 0, T_wall), rounded once from an
+ *    exact value.  Left/right edges are periodic.
+ *
+ * POPULATION ORDER.  l = 0 is xi = (0,0).  For k = 0..17, l = 2k+1 is +R_k and
+ * l = 2k+2 is -R_k with R = (1,0) (0,1) (1,1) (-1,1) (2,0) (0,2) (2,1) (1,2)
+ * (-1,2) (-2,1) (2,2) (-2,2) (3,0) (0,3) (3,1) (1,3) (-1,3) (-3,1).
+ *
+ * STATE LAYOUT.  A lattice state is one contiguous device buffer of
+ * 37 planes; plane l holds rows y = -3 .. ly+2 (three halo rows below and
+ * above the ly physical rows), each row lx elements, x fastest:
+ *     f[(l * (ly + 6) + (y + 3)) * lx + x]
+ * (the structure-of-arrays layout of Sect. 4, Fig. "streamscheme").
+ * Element type: double (LBM_FP64), or float holding f_l - w_l rho0
+ * (LBM_FP32_SHIFTED).  Halo rows are never read as data and never written
+ * by a step: they may hold anything, NaN included.
+ * Macroscopic fields are double arrays of ly rows of lx, x fastest.
+ *
+ * OWNERSHIP.  The caller owns every lattice and field buffer (device memory
+ * unless stated otherwise) and the CUDA stream.  A context allocates one
+ * small device block of its own (status word and flags, freed by
+ * lbm_destroy); a batch additionally allocates its small parameter table.
+ * All work is enqueued asynchronously on the context's stream; a call
+ * returns once its work is enqueued.
+ *
+ * ERRORS.  Every int-returning call returns LBM_OK (0) or a negative code;
+ * lbm_last_error() gives a message.  Invalid arguments are rejected before
+ * any work is enqueued.  Errors of asynchronous work appear at a later call
+ * or at lbm_status().  No call throws or aborts.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_NPOP 37
+#define LBM_HALO 3
+
+enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID = -1,   /* bad argument (NULL, out of range, bad mode)     */
+  LBM_ERR_SIZE = -2,      /* buffer size does not match the lattice          */
+  LBM_ERR_CUDA = -3,      /* a CUDA runtime call failed                      */
+  LBM_ERR_NONFINITE = -4, /* reserved: state check found NaN/Inf             */
+  LBM_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                   */
+  LBM_ERR_STATE = -6      /* call not valid in the object's current state    */
+};
+
+enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+enum { LBM_FLAG_PERIODIC_Y = 1 };  /* test mode: no walls, y periodic */
+
+typedef struct lbm_params {
+  int32_t lx;         /* physical columns, >= 3 (periodic)                    */
+  int32_t ly;         /* physical rows, >= 6 (walls at both ends)             */
+  int32_t precision;  /* LBM_FP64 or LBM_FP32_SHIFTED                         */
+  int32_t flags;      /* LBM_FLAG_* bits                                      */
+  double tau;         /* relaxation time, > 0.5 (eq. 1)                        */
+  double g;           /* gravity magnitude, acting along -y                    */
+  double t_top;       /* wall temperature of the top rows                      */
+  double t_bottom;    /* wall temperature of the bottom rows                   */
+  double rho0;        /* density of the FP32 shift f_l - w_l rho0              */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of one lattice state buffer: 37 * (ly + 6) * lx * element size.
+ * Returns 0 for invalid parameters. */
+size_t lbm_state_bytes(const lbm_params* p);
+
+/* Create a context over two caller-owned device state buffers f_a, f_b of
+ * `bytes` each (ping-pong; f_a holds the current state after creation).
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  Solves the
+ * D2Q37 quadrature and the wall ratios on the host.  *out is NULL on error. */
+int lbm_create(lbm_ctx** out, const lbm_params* p, void* f_a, void* f_b,
+               size_t bytes, void* stream);
+
+/* Release the context and its small device block; the caller's buffers are
+ * untouched.  NULL is accepted. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last error on this context (never NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Change the stream used by later calls. */
+int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Initial assignment of the populations (Sect. 2: "an initial assignment of
+ * the populations"): current state := f^eq(rho, u, T) at every physical
+ * site.  rho, ux, uy, T: device arrays [ly][lx]. */
+int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux,
+             const double* uy, const double* T);
+
+/* Advance n >= 0 time steps (Sect. 2: propagate, bc, collide; eq. 1).  Each
+ * step is one fused kernel launch reading the current buffer and writing the
+ * other; the buffers then swap roles. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Device pointer of the buffer holding the current state. */
+void* lbm_current(const lbm_ctx* ctx);
+
+/* Macroscopic fields of eq. (2) of the state f (NULL = current state), as
+ * raw moments of the stored populations: rho, u = j / rho,
+ * T = (E / rho - |u|^2) / D.  Outputs: device arrays [ly][lx]. */
+int lbm_moments(lbm_ctx* ctx, const void* f, double* rho, double* ux,
+                double* uy, double* T);
+
+/* Checkpoint / restore: copy the current state to / from a caller buffer of
+ * lbm_state_bytes() (device memory, or host memory the CUDA runtime can
+ * address, e.g. pinned). */
+int lbm_get_state(lbm_ctx* ctx, void* dst);
+int lbm_set_state(lbm_ctx* ctx, const void* src);
+
+/* propagate followed by bc only (Sect. 2, first two kernels), from state src
+ * to state dst (both in the context's precision; must not alias).  The
+ * current state is not changed. */
+int lbm_propagate_bc(lbm_ctx* ctx, const void* src, void* dst);
+
+/* One step of the discrete adjoint (transpose of the Jacobian of one step,
+ * eq. 1 with propagate, bc and collide, linearised at state f_t):
+ *   lam_out = P^T B^T C^T lam_in.
+ * f_t: state in the context's precision (FP32 states are decoded and the
+ * Jacobian of the float64 step is taken there).  lam_in, lam_out: double
+ * arrays in the FP64 state layout; must not alias.  The halo rows of lam_out
+ * are used as scratch and hold no data afterwards. */
+int lbm_adjoint_step(lbm_ctx* ctx, const void* f_t, const double* lam_in,
+                     double* lam_out);
+
+/* Vector-Jacobian product of lbm_moments at state f:
+ *   lam_out_l = d rho/d f_l g_rho + d u/d f_l . g_u + d T/d f_l g_T
+ * (eq. 2).  Cotangent fields [ly][lx]; any of them may be NULL (zero).
+ * lam_out: double array in the FP64 state layout. */
+int lbm_moments_vjp(lbm_ctx* ctx, const void* f, const double* g_rho,
+                    const double* g_ux, const double* g_uy, const double* g_T,
+                    double* lam_out);
+
+/* Vector-Jacobian product of lbm_init: for lam in the FP64 state layout,
+ * g_x = sum_l lam_l d f^eq_l / d x at (rho, u, T) for x in {rho, ux, uy, T}.
+ * Outputs [ly][lx]; any output may be NULL (not computed). */
+int lbm_init_vjp(lbm_ctx* ctx, const double* rho, const double* ux,
+                 const double* uy, const double* T, const double* lam,
+                 double* g_rho, double* g_ux, double* g_uy, double* g_T);
+
+/* Check that every physical population of state f (NULL = current) is
+ * finite.  Synchronises the stream; *ok = 1 if finite, else 0. */
+int lbm_check_finite(lbm_ctx* ctx, const void* f, int* ok);
+
+/* Synchronise the stream and return the first error of asynchronous work:
+ * a CUDA error (LBM_ERR_CUDA) or the device status word (LBM_ERR_*). */
+int lbm_status(lbm_ctx* ctx);
+
+/* Copy of the float64 constants the context derived: r, the 37 weights w_l
+ * and the wall ratios q_l of the bottom and top walls (zero where slot l is
+ * not an unknown of that wall).  Any pointer may be NULL. */
+int lbm_constants(const lbm_ctx* ctx, double* r, double* w37,
+                  double* q_bottom37, double* q_top37);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,319 @@
+// C ABI of liblbm.so: contexts, argument checking and kernel launches.
+// Declarations and their documentation: include/lbm.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a,
+                        cudaStream_t s);
+cudaError_t launch_init(int prec, void* dst, const double* rho, const double* ux, const double* uy,
+                        const double* T, const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_moments(int prec, const void* src, double* rho, double* ux, double* uy, double* T,
+                           const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_finite(int prec, const void* src, const LatticeArgs& a, unsigned int* flag,
+                          cudaStream_t s);
+cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, double* lam_out,
+                           const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux,
+                               const double* g_uy, const double* g_T, double* lam_out,
+                               const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_init_vjp(const double* rho, const double* ux, const double* uy, const double* T,
+                            const double* lam, double* g_rho, double* g_ux, double* g_uy,
+                            double* g_T, const LatticeArgs& a, cudaStream_t s);
+
+namespace {
+std::once_flag g_quad_once;
+Quadrature g_quad;
+int g_quad_rc = -1;
+char g_quad_err[256] = "";
+
+const Quadrature* quadrature(char* err, size_t errlen) {
+  std::call_once(g_quad_once, [] { g_quad_rc = solve_quadrature(&g_quad, g_quad_err, sizeof g_quad_err); });
+  if (g_quad_rc != 0) {
+    std::snprintf(err, errlen, "%s", g_quad_err);
+    return nullptr;
+  }
+  return &g_quad;
+}
+}  // namespace
+
+// Fill the per-launch constants of a lattice.  Returns 0 or an error code
+// with a message in err.
+int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t errlen) {
+  if (p.lx < 3 || p.ly < 6) {
+    std::snprintf(err, errlen, "lattice %d x %d too small (need lx >= 3, ly >= 6)", p.lx, p.ly);
+    return LBM_ERR_INVALID;
+  }
+  if ((long long)p.lx * (p.ly + 2 * HALO) > (1LL << 40)) {
+    std::snprintf(err, errlen, "lattice too large");
+    return LBM_ERR_INVALID;
+  }
+  if (p.precision != LBM_FP64 && p.precision != LBM_FP32_SHIFTED) {
+    std::snprintf(err, errlen, "unknown precision %d", p.precision);
+    return LBM_ERR_INVALID;
+  }
+  if (!(p.tau > 0.5) || !std::isfinite(p.tau) || !std::isfinite(p.g) || !std::isfinite(p.t_top) ||
+      !std::isfinite(p.t_bottom) || !std::isfinite(p.rho0) || !(p.t_top > 0) || !(p.t_bottom > 0)) {
+    std::snprintf(err, errlen, "invalid physical parameters (need tau > 0.5, finite g, T_wall > 0)");
+    return LBM_ERR_INVALID;
+  }
+  if (p.flags & ~LBM_FLAG_PERIODIC_Y) {
+    std::snprintf(err, errlen, "unknown flags 0x%x", p.flags);
+    return LBM_ERR_INVALID;
+  }
+  const Quadrature* q = quadrature(err, errlen);
+  if (!q) return LBM_ERR_INVALID;
+  std::memset(a, 0, sizeof *a);
+  a->lx = p.lx;
+  a->ly = p.ly;
+  a->plane = (long long)(p.ly + 2 * HALO) * p.lx;
+  a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;
+  a->tau = p.tau;
+  a->omega = 1.0 / p.tau;
+  a->omc = 1.0 - a->omega;
+  a->r = q->r;
+  a->r2 = q->r * q->r;
+  a->inv_r2 = q->y;
+  a->tau_g_xi = p.tau * p.g / q->r;
+  a->tshift = p.tau * (1.0 - p.tau) * p.g * p.g / 2.0 - 1.0;
+  a->rho0 = p.rho0;
+  for (int j = 0; j < NSHELL; ++j) {
+    a->w_shell[j] = q->w_shell[j];
+    a->c2_shell[j] = q->c2_shell[j];
+  }
+  wall_ratios(*q, p.t_bottom, 0, a->q_bot);
+  wall_ratios(*q, p.t_top, 1, a->q_top);
+  for (int l = 0; l < NPOP; ++l) {
+    a->w_rho0[l] = q->w[l] * p.rho0;
+    a->w_rho0_f[l] = (float)a->w_rho0[l];
+  }
+  return LBM_OK;
+}
+
+size_t element_size(int precision) { return precision == LBM_FP32_SHIFTED ? sizeof(float) : sizeof(double); }
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+  lbm_params p;
+  LatticeArgs args;
+  void* buf[2];
+  int cur;
+  size_t bytes;
+  cudaStream_t stream;
+  unsigned int* dev;  // [0] status word, [1] finite flag
+  char err[512];
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(c->err, sizeof c->err, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_check(lbm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LBM_OK;
+  return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_state_bytes(const lbm_params* p) {
+  if (!p || p->lx < 3 || p->ly < 6) return 0;
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED) return 0;
+  return (size_t)NPOP * (size_t)(p->ly + 2 * HALO) * (size_t)p->lx * element_size(p->precision);
+}
+
+int lbm_create(lbm_ctx** out, const lbm_params* p, void* f_a, void* f_b, size_t bytes, void* stream) {
+  if (!out) return LBM_ERR_INVALID;
+  *out = nullptr;
+  if (!p || !f_a || !f_b || f_a == f_b) return LBM_ERR_INVALID;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_INVALID;
+  c->p = *p;
+  int rc = make_lattice_args(*p, &c->args, c->err, sizeof c->err);
+  if (rc != LBM_OK) {
+    delete c;
+    return rc;
+  }
+  if (bytes != lbm_state_bytes(p)) {
+    delete c;
+    return LBM_ERR_SIZE;
+  }
+  if (!aligned(f_a, element_size(p->precision)) || !aligned(f_b, element_size(p->precision))) {
+    delete c;
+    return LBM_ERR_INVALID;
+  }
+  c->buf[0] = f_a;
+  c->buf[1] = f_b;
+  c->cur = 0;
+  c->bytes = bytes;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaMalloc(&c->dev, 2 * sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return LBM_ERR_CUDA;
+  }
+  c->args.status = c->dev;
+  if (cudaMemsetAsync(c->dev, 0, 2 * sizeof(unsigned int), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->dev);
+    delete c;
+    return LBM_ERR_CUDA;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->dev) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->dev);
+  }
+  delete c;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : "null context"; }
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (!c) return LBM_ERR_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!rho || !ux || !uy || !T) return fail(c, LBM_ERR_INVALID, "lbm_init: NULL field");
+  return cuda_check(c, launch_init(c->p.precision, c->buf[c->cur], rho, ux, uy, T, c->args, c->stream),
+                    "lbm_init");
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (!c) return LBM_ERR_INVALID;
+  if (n < 0) return fail(c, LBM_ERR_INVALID, "lbm_step: n < 0");
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = launch_step(c->p.precision, true, c->buf[c->cur], c->buf[1 - c->cur], c->args, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "lbm_step");
+    c->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+void* lbm_current(const lbm_ctx* c) { return c ? c->buf[c->cur] : nullptr; }
+
+int lbm_moments(lbm_ctx* c, const void* f, double* rho, double* ux, double* uy, double* T) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!rho && !ux && !uy && !T) return fail(c, LBM_ERR_INVALID, "lbm_moments: no output");
+  if (!f) f = c->buf[c->cur];
+  return cuda_check(c, launch_moments(c->p.precision, f, rho, ux, uy, T, c->args, c->stream), "lbm_moments");
+}
+
+int lbm_get_state(lbm_ctx* c, void* dst) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!dst) return fail(c, LBM_ERR_INVALID, "lbm_get_state: NULL");
+  return cuda_check(c, cudaMemcpyAsync(dst, c->buf[c->cur], c->bytes, cudaMemcpyDefault, c->stream),
+                    "lbm_get_state");
+}
+
+int lbm_set_state(lbm_ctx* c, const void* src) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!src) return fail(c, LBM_ERR_INVALID, "lbm_set_state: NULL");
+  return cuda_check(c, cudaMemcpyAsync(c->buf[c->cur], src, c->bytes, cudaMemcpyDefault, c->stream),
+                    "lbm_set_state");
+}
+
+int lbm_propagate_bc(lbm_ctx* c, const void* src, void* dst) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!src || !dst || src == dst) return fail(c, LBM_ERR_INVALID, "lbm_propagate_bc: bad buffers");
+  return cuda_check(c, launch_step(c->p.precision, false, src, dst, c->args, c->stream), "lbm_propagate_bc");
+}
+
+int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const double* lam_in, double* lam_out) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!f_t || !lam_in || !lam_out || (const void*)lam_in == (const void*)lam_out)
+    return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step: bad buffers");
+  return cuda_check(c, launch_adjoint(c->p.precision, f_t, lam_in, lam_out, c->args, c->stream),
+                    "lbm_adjoint_step");
+}
+
+int lbm_moments_vjp(lbm_ctx* c, const void* f, const double* g_rho, const double* g_ux, const double* g_uy,
+                    const double* g_T, double* lam_out) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!f || !lam_out) return fail(c, LBM_ERR_INVALID, "lbm_moments_vjp: bad buffers");
+  return cuda_check(c, launch_moments_vjp(c->p.precision, f, g_rho, g_ux, g_uy, g_T, lam_out, c->args, c->stream),
+                    "lbm_moments_vjp");
+}
+
+int lbm_init_vjp(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T,
+                 const double* lam, double* g_rho, double* g_ux, double* g_uy, double* g_T) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!rho || !ux || !uy || !T || !lam) return fail(c, LBM_ERR_INVALID, "lbm_init_vjp: NULL input");
+  return cuda_check(c, launch_init_vjp(rho, ux, uy, T, lam, g_rho, g_ux, g_uy, g_T, c->args, c->stream),
+                    "lbm_init_vjp");
+}
+
+int lbm_check_finite(lbm_ctx* c, const void* f, int* ok) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!ok) return fail(c, LBM_ERR_INVALID, "lbm_check_finite: NULL ok");
+  if (!f) f = c->buf[c->cur];
+  int rc = cuda_check(c, cudaMemsetAsync(c->dev + 1, 0, sizeof(unsigned int), c->stream), "lbm_check_finite");
+  if (rc) return rc;
+  rc = cuda_check(c, launch_finite(c->p.precision, f, c->args, c->dev + 1, c->stream), "lbm_check_finite");
+  if (rc) return rc;
+  unsigned int flag = 0;
+  rc = cuda_check(c, cudaMemcpyAsync(&flag, c->dev + 1, sizeof flag, cudaMemcpyDeviceToHost, c->stream),
+                  "lbm_check_finite");
+  if (rc) return rc;
+  rc = cuda_check(c, cudaStreamSynchronize(c->stream), "lbm_check_finite");
+  if (rc) return rc;
+  *ok = flag ? 0 : 1;
+  return LBM_OK;
+}
+
+int lbm_status(lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID;
+  int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "lbm_status");
+  if (rc) return rc;
+  unsigned int w = 0;
+  rc = cuda_check(c, cudaMemcpy(&w, c->dev, sizeof w, cudaMemcpyDeviceToHost), "lbm_status");
+  if (rc) return rc;
+  if (w) return fail(c, LBM_ERR_TIMEOUT, "device status word 0x%x", w);
+  return LBM_OK;
+}
+
+int lbm_constants(const lbm_ctx* c, double* r, double* w37, double* q_bottom37, double* q_top37) {
+  if (!c) return LBM_ERR_INVALID;
+  char err[128];
+  const Quadrature* q = quadrature(err, sizeof err);
+  if (!q) return LBM_ERR_INVALID;
+  if (r) *r = q->r;
+  for (int l = 0; l < NPOP; ++l) {
+    if (w37) w37[l] = q->w[l];
+    if (q_bottom37) q_bottom37[l] = c->args.q_bot[l];
+    if (q_top37) q_top37[l] = c->args.q_top[l];
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+// Device building blocks of the D2Q37 step: pull gather with periodic x,
+// thermal walls, and the float64 / float32-shifted BGK collide.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+__device__ __forceinline__ int wrap_x(int xs, int lx) {
+  xs = xs < 0 ? xs + lx : xs;
+  return xs >= lx ? xs - lx : xs;
+}
+
+// Element offset of (l, y, x) in a state buffer (y physical, may be a halo row).
+__device__ __forceinline__ long long sidx(const LatticeArgs& a, int l, int y, int x) {
+  return (long long)l * a.plane + (long long)(y + HALO) * a.lx + x;
+}
+
+// propagate (Sect. 2, eq. 1 first term): f_l <- src_l(x - xi_l), periodic in x;
+// in y the source may be a halo row (replaced by the walls) or, in the
+// periodic-y test mode, wraps.
+template <typename T>
+__device__ __forceinline__ void pull(const T* __restrict__ src, int x, int y,
+                                     const LatticeArgs& a, T (&f)[NPOP]) {
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) {
+    const int xs = wrap_x(x - vx(l), a.lx);
+    int ys = y - vy(l);
+    if (a.periodic_y) ys = ys < 0 ? ys + a.ly : (ys >= a.ly ? ys - a.ly : ys);
+    f[l] = __ldg(src + sidx(a, l, ys, xs));
+  }
+}
+
+// Mass M(x) that left through the bottom (top) wall during propagate and lands
+// in column x, summed in the fixed order: l ascending, then source row
+// ascending; round-to-nearest adds without contraction.  `decode` maps a
+// stored element of population l to its float64 population value.
+template <bool TOP, typename T, typename Decode>
+__device__ __forceinline__ double lost_mass(const T* __restrict__ src, int x,
+                                            const LatticeArgs& a, Decode decode) {
+  double M = 0.0;
+  bool first = true;
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      // bottom: source row y0 = e, lost if y0 + xi_y < 0;
+      // top:    source row y0 = ly - 3 + e, lost if y0 + xi_y >= ly.
+      const bool lost = TOP ? (e + vy(l) >= 3) : (e + vy(l) < 0);
+      if (lost) {
+        const int y0 = TOP ? a.ly - 3 + e : e;
+        const double v = decode(l, __ldg(src + sidx(a, l, y0, wrap_x(x - vx(l), a.lx))));
+        M = first ? v : __dadd_rn(M, v);
+        first = false;
+      }
+    }
+  }
+  return M;
+}
+
+// Replace the unknown slots of a wall row by M(x) q_l (Sect. 2, bc).
+// `encode` maps a float64 population value of population l to storage.
+template <typename S, typename F, typename Decode, typename Encode>
+__device__ __forceinline__ void walls(const S* __restrict__ src, int x, int y,
+                                      const LatticeArgs& a, F (&f)[NPOP],
+                                      Decode decode, Encode encode) {
+  if (a.periodic_y) return;
+  if (y < 3) {
+    const double M = lost_mass<false>(src, x, a, decode);
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l)
+      if (vy(l) > 0 && vy(l) > y) f[l] = encode(l, __dmul_rn(M, a.q_bot[l]));
+  } else if (y >= a.ly - 3) {
+    const double M = lost_mass<true>(src, x, a, decode);
+    const int d = a.ly - 1 - y;  // row offset from the top wall
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l)
+      if (vy(l) < 0 && -vy(l) > d) f[l] = encode(l, __dmul_rn(M, a.q_top[l]));
+  }
+}
+
+// Per-site coefficients of the 4th-order Hermite equilibrium, written as a
+// polynomial in cu = c.u' for each shell (D = 2, theta = T' - 1, U2 = |u'|^2):
+//   P = A0 + A1 cu + A2 cu^2 + cu^3 / 6 + cu^4 / 24,
+//   A0 = B00 + B01 c2 + B02 c2^2,  A1 = B10 + B11 c2,  A2 = B20 + B21 c2.
+struct EqCoef {
+  double B00, B01, B02, B10, B11, B20, B21;
+};
+
+__device__ __forceinline__ EqCoef eq_coef(double U2, double theta) {
+  EqCoef c;
+  c.B20 = fma(-1.5, theta, fma(-0.25, U2, 0.5));
+  c.B21 = 0.25 * theta;
+  c.B10 = fma(-2.0, theta, fma(-0.5, U2, 1.0));
+  c.B11 = 0.5 * theta;
+  c.B00 = fma(theta, (U2 - 1.0) + theta, fma(U2, fma(0.125, U2, -0.5), 1.0));
+  c.B01 = theta * (fma(-0.25, U2, 0.5) - theta);
+  c.B02 = 0.125 * (theta * theta);
+  return c;
+}
+
+// cu = xi_k . v for the pair representative k (v = r u' in xi units).
+template <typename R>
+__device__ __forceinline__ R pair_cu(int k, R v_x, R v_y) {
+  const int ax = rep_x(k), ay = rep_y(k);
+  if (ax == 0) return ay == 1 ? v_y : (R)ay * v_y;
+  if (ay == 0) return ax == 1 ? v_x : (R)ax * v_x;
+  const R ty = ay == 1 ? v_y : (R)ay * v_y;
+  return ax == 1 ? v_x + ty : (ax == -1 ? ty - v_x : fma((R)ax, v_x, ty));
+}
+
+// Moment sums of 37 values in float64 using the (+,-) pairing:
+// rho = sum f, Jx = sum xi_x f, Jy = sum xi_y f, Exi = sum |xi|^2 f.
+struct Moments {
+  double rho, Jx, Jy, Exi;
+};
+
+template <typename Get>
+__device__ __forceinline__ Moments moment_sums(Get get) {
+  double sh[NSHELL];
+#pragma unroll
+  for (int j = 0; j < NSHELL; ++j) sh[j] = -0.0;
+  double Jx = -0.0, Jy = -0.0;
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const double p = get(2 * k + 1), m = get(2 * k + 2);
+    const double s = p + m, d = p - m;
+    sh[pair_shell(k)] += s;
+    if (rep_x(k) != 0) Jx = rep_x(k) == 1 ? Jx + d : rep_x(k) == -1 ? Jx - d : fma((double)rep_x(k), d, Jx);
+    if (rep_y(k) != 0) Jy = rep_y(k) == 1 ? Jy + d : fma((double)rep_y(k), d, Jy);
+  }
+  Moments mo;
+  mo.rho = ((get(0) + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
+  mo.Exi = fma(10.0, sh[7], fma(9.0, sh[6], fma(8.0, sh[5], fma(5.0, sh[4], fma(4.0, sh[3], fma(2.0, sh[2], sh[1]))))));
+  mo.Jx = Jx;
+  mo.Jy = Jy;
+  return mo;
+}
+
+// Site state derived from the moments: velocity in xi units and temperature.
+struct SiteFields {
+  double rho, inv, ux, uy, T;  // u = r (ux, uy)
+};
+
+__device__ __forceinline__ SiteFields site_fields(const Moments& m, const LatticeArgs& a) {
+  SiteFields s;
+  s.rho = m.rho;
+  s.inv = 1.0 / m.rho;
+  s.ux = m.Jx * s.inv;
+  s.uy = m.Jy * s.inv;
+  s.T = 0.5 * a.r2 * fma(m.Exi, s.inv, -fma(s.ux, s.ux, s.uy * s.uy));
+  return s;
+}
+
+// BGK collide in float64 (eq. 1) with the gravity equilibrium shift.
+__device__ __forceinline__ void collide_fp64(double (&f)[NPOP], const LatticeArgs& a) {
+  const Moments mo = moment_sums([&](int l) { return f[l]; });
+  const SiteFields sf = site_fields(mo, a);
+  const double theta = sf.T + a.tshift;
+  const double uys = sf.uy - a.tau_g_xi;
+  const double v_x = a.r2 * sf.ux, v_y = a.r2 * uys;
+  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
+  const EqCoef B = eq_coef(U2, theta);
+  const double wr = a.omega * sf.rho;
+  f[0] = fma(a.omc, f[0], (wr * a.w_shell[0]) * B.B00);
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int j = pair_shell(k);
+    const double c2 = a.c2_shell[j];
+    const double A0 = fma(c2, fma(c2, B.B02, B.B01), B.B00);
+    const double A1 = fma(B.B11, c2, B.B10);
+    const double A2 = fma(B.B21, c2, B.B20);
+    const double sc = wr * a.w_shell[j];
+    const double cu = pair_cu<double>(k, v_x, v_y);
+    const double cu2 = cu * cu;
+    const double E = fma(cu2, fma(cu2, 1.0 / 24.0, A2), A0);
+    const double O = cu * fma(cu2, 1.0 / 6.0, A1);
+    f[2 * k + 1] = fma(a.omc, f[2 * k + 1], sc * (E + O));
+    f[2 * k + 2] = fma(a.omc, f[2 * k + 2], sc * (E - O));
+  }
+}
+
+// BGK collide on float32 deviations d_l = f_l - w_l rho0: the moment sums,
+// the velocity, the temperature and the temperature-dependent equilibrium
+// coefficients in float64; the per-population polynomial and relaxation in
+// float32:  d_l <- (1 - omega) d_l + omega (f^eq_l - w_l rho0).
+__device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
+  Moments mo = moment_sums([&](int l) { return (double)d[l]; });
+  // add back the shift: sum w rho0 = rho0, sum w xi = 0, sum w |xi|^2 = D / r^2
+  mo.rho += a.rho0;
+  mo.Exi = fma(2.0 * a.inv_r2, a.rho0, mo.Exi);
+  const SiteFields sf = site_fields(mo, a);
+  const double theta = sf.T + a.tshift;
+  const double uys = sf.uy - a.tau_g_xi;
+  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
+  const EqCoef B = eq_coef(U2, theta);
+  const double rho = sf.rho;
+  // float64 -> float32 hand-over of the site coefficients
+  const float v_x = (float)(a.r2 * sf.ux), v_y = (float)(a.r2 * uys);
+  const float b10 = (float)B.B10, b11 = (float)B.B11, b20 = (float)B.B20, b21 = (float)B.B21;
+  const float rb00 = (float)fma(rho, B.B00, -a.rho0);  // rho B00 - rho0
+  const float rb01 = (float)(rho * B.B01), rb02 = (float)(rho * B.B02);
+  const float om = (float)a.omega, omc = (float)a.omc;
+  const float wr = (float)(a.omega * rho);
+  d[0] = fmaf(omc, d[0], om * (float)a.w_shell[0] * rb00);
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int j = pair_shell(k);
+    const float c2 = (float)a.c2_shell[j];
+    const float w = (float)a.w_shell[j];
+    const float A1 = fmaf(b11, c2, b10);
+    const float A2 = fmaf(b21, c2, b20);
+    const float alpha = wr * w;                                   // omega w rho
+    const float beta = om * w * fmaf(c2, fmaf(c2, rb02, rb01), rb00);  // omega w (rho A0 - rho0)
+    const float cu = pair_cu<float>(k, v_x, v_y);
+    const float cu2 = cu * cu;
+    const float E = fmaf(alpha * cu2, fmaf(cu2, 1.0f / 24.0f, A2), beta);
+    const float O = alpha * cu * fmaf(cu2, 1.0f / 6.0f, A1);
+    d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
+    d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
+  }
+}
+
+// Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.
+__device__ __forceinline__ void equilibrium(double rho, double ux, double uy, double T,
+                                            const LatticeArgs& a, double (&f)[NPOP]) {
+  const double theta = T - 1.0;
+  const double U2 = fma(ux, ux, uy * uy);
+  const double v_x = a.r * ux, v_y = a.r * uy;
+  const EqCoef B = eq_coef(U2, theta);
+  f[0] = (rho * a.w_shell[0]) * B.B00;
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int j = pair_shell(k);
+    const double c2 = a.c2_shell[j];
+    const double A0 = fma(c2, fma(c2, B.B02, B.B01), B.B00);
+    const double A1 = fma(B.B11, c2, B.B10);
+    const double A2 = fma(B.B21, c2, B.B20);
+    const double sc = rho * a.w_shell[j];
+    const double cu = pair_cu<double>(k, v_x, v_y);
+    const double cu2 = cu * cu;
+    const double E = fma(cu2, fma(cu2, 1.0 / 24.0, A2), A0);
+    const double O = cu * fma(cu2, 1.0 / 6.0, A1);
+    f[2 * k + 1] = sc * (E + O);
+    f[2 * k + 2] = sc * (E - O);
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,175 @@
+"""Python front end of the D2Q37 library: a lattice whose state lives in HBM.
+
+PyTorch supplies device memory and the stream; every step of the method runs
+in liblbm.so's CUDA kernels (include/lbm.h documents each call).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+NPOP = 37
+HALO = 3
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _field(v, ly, lx, device):
+    """A float64 (ly, lx) contiguous device tensor from a tensor or array."""
+    if isinstance(v, torch.Tensor):
+        t = v.to(device=device, dtype=torch.float64)
+    else:
+        t = torch.as_tensor(np.asarray(v, dtype=np.float64), device=device)
+    t = t.contiguous()
+    if tuple(t.shape) != (ly, lx):
+        raise ValueError(f"field shape {tuple(t.shape)} != {(ly, lx)}")
+    return t
+
+
+class Lattice:
+    """One D2Q37 lattice with walls at the top and bottom rows and periodic x.
+
+    State buffers are (37, ly + 6, lx) tensors (three halo rows on each side,
+    x fastest); dtype float64, or float32 holding f_l - w_l rho0 when
+    ``precision="fp32"``.
+    """
+
+    def __init__(self, lx: int, ly: int, tau: float, g: float = 0.0, t_top: float = 1.0,
+                 t_bottom: float = 1.0, precision: str = "fp64", rho0: float = 1.0,
+                 periodic_y: bool = False, device=None, stream=None):
+        self.lib = L.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.lx, self.ly = int(lx), int(ly)
+        self.precision = precision
+        prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED}[precision]
+        self.dtype = torch.float64 if prec == L.LBM_FP64 else torch.float32
+        self.params = L.LbmParams(self.lx, self.ly, prec, L.LBM_FLAG_PERIODIC_Y if periodic_y else 0,
+                                  float(tau), float(g), float(t_top), float(t_bottom), float(rho0))
+        self.tau, self.g, self.t_top, self.t_bottom, self.rho0 = tau, g, t_top, t_bottom, rho0
+        self.periodic_y = periodic_y
+        nbytes = self.lib.lbm_state_bytes(ctypes.byref(self.params))
+        if nbytes == 0:
+            raise L.LBMError(L.LBM_ERR_INVALID, "invalid lattice parameters")
+        self.nbytes = nbytes
+        self.shape = (NPOP, self.ly + 2 * HALO, self.lx)
+        self.buffers = [torch.full(self.shape, float("nan"), dtype=self.dtype, device=self.device)
+                        for _ in range(2)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = ctypes.c_void_p()
+        rc = self.lib.lbm_create(ctypes.byref(ctx), ctypes.byref(self.params), _ptr(self.buffers[0]),
+                                 _ptr(self.buffers[1]), nbytes, ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise L.LBMError(rc, "lbm_create failed (invalid parameters, size or alignment)")
+        self.ctx = ctx
+
+    # ------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            msg = self.lib.lbm_last_error(self.ctx)
+            raise L.LBMError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_state(self, fill=float("nan")):
+        return torch.full(self.shape, fill, dtype=self.dtype, device=self.device)
+
+    def new_cotangent(self, fill=float("nan")):
+        return torch.full((NPOP, self.ly + 2 * HALO, self.lx), fill, dtype=torch.float64, device=self.device)
+
+    # ------------------------------------------------------------------
+    def init(self, rho, ux, uy, T):
+        """Current state := f^eq(rho, u, T) (fields (ly, lx))."""
+        f = [_field(v, self.ly, self.lx, self.device) for v in (rho, ux, uy, T)]
+        self._check(self.lib.lbm_init(self.ctx, *[_ptr(t) for t in f]))
+        self._keep = f  # alive until the next call on this stream
+        return self
+
+    def step(self, n: int = 1):
+        self._check(self.lib.lbm_step(self.ctx, int(n)))
+        return self
+
+    def state(self) -> torch.Tensor:
+        """The buffer holding the current state (a view; it changes role at each step)."""
+        ptr = self.lib.lbm_current(self.ctx)
+        return self.buffers[0] if ptr == self.buffers[0].data_ptr() else self.buffers[1]
+
+    def set_state(self, src: torch.Tensor):
+        if src.dtype != self.dtype or tuple(src.shape) != self.shape:
+            raise ValueError("state dtype/shape mismatch")
+        self._check(self.lib.lbm_set_state(self.ctx, _ptr(src.contiguous())))
+        return self
+
+    def get_state(self, dst: torch.Tensor):
+        if dst.dtype != self.dtype or tuple(dst.shape) != self.shape or not dst.is_contiguous():
+            raise ValueError("state dtype/shape mismatch")
+        self._check(self.lib.lbm_get_state(self.ctx, _ptr(dst)))
+        return dst
+
+    def moments(self, f: torch.Tensor | None = None):
+        out = [torch.empty((self.ly, self.lx), dtype=torch.float64, device=self.device) for _ in range(4)]
+        self._check(self.lib.lbm_moments(self.ctx, _ptr(f), *[_ptr(t) for t in out]))
+        return tuple(out)
+
+    def propagate_bc(self, src: torch.Tensor, dst: torch.Tensor | None = None):
+        if dst is None:
+            dst = self.new_state()
+        self._check(self.lib.lbm_propagate_bc(self.ctx, _ptr(src), _ptr(dst)))
+        return dst
+
+    def adjoint_step(self, f_t: torch.Tensor, lam_in: torch.Tensor, lam_out: torch.Tensor | None = None):
+        if lam_out is None:
+            lam_out = self.new_cotangent()
+        self._check(self.lib.lbm_adjoint_step(self.ctx, _ptr(f_t), _ptr(lam_in), _ptr(lam_out)))
+        return lam_out
+
+    def moments_vjp(self, f, g_rho=None, g_ux=None, g_uy=None, g_T=None, lam_out=None):
+        if lam_out is None:
+            lam_out = self.new_cotangent()
+        gs = [None if g is None else _field(g, self.ly, self.lx, self.device) for g in (g_rho, g_ux, g_uy, g_T)]
+        self._check(self.lib.lbm_moments_vjp(self.ctx, _ptr(f), *[_ptr(g) for g in gs], _ptr(lam_out)))
+        self._keep = gs
+        return lam_out
+
+    def init_vjp(self, rho, ux, uy, T, lam):
+        f = [_field(v, self.ly, self.lx, self.device) for v in (rho, ux, uy, T)]
+        out = [torch.empty((self.ly, self.lx), dtype=torch.float64, device=self.device) for _ in range(4)]
+        self._check(self.lib.lbm_init_vjp(self.ctx, *[_ptr(t) for t in f], _ptr(lam), *[_ptr(t) for t in out]))
+        self._keep = f
+        return tuple(out)
+
+    def check_finite(self, f: torch.Tensor | None = None) -> bool:
+        ok = ctypes.c_int(0)
+        self._check(self.lib.lbm_check_finite(self.ctx, _ptr(f), ctypes.byref(ok)))
+        return bool(ok.value)
+
+    def status(self) -> int:
+        return self.lib.lbm_status(self.ctx)
+
+    def constants(self):
+        r = ctypes.c_double()
+        arrs = [(ctypes.c_double * NPOP)() for _ in range(3)]
+        self._check(self.lib.lbm_constants(self.ctx, ctypes.byref(r), *arrs))
+        return r.value, *[np.array(a[:]) for a in arrs]

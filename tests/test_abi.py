@@ -1,0 +1,63 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function its headers declare (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(INCLUDE):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1703_00186_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def test_headers_declare_the_core_calls():
+    names = declared_functions()
+    for n in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_adjoint_step",
+              "lbm_propagate_bc", "lbm_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_state_bytes_and_argument_checks_need_no_gpu(lib):
+    from paper_1703_00186_gb300 import _lib as L
+    p = L.LbmParams(64, 128, L.LBM_FP64, 0, 0.8, 1e-4, 0.5, 1.5, 1.0)
+    assert lib.lbm_state_bytes(ctypes.byref(p)) == 37 * 134 * 64 * 8
+    p32 = L.LbmParams(64, 128, L.LBM_FP32_SHIFTED, 0, 0.8, 1e-4, 0.5, 1.5, 1.0)
+    assert lib.lbm_state_bytes(ctypes.byref(p32)) == 37 * 134 * 64 * 4
+    bad = L.LbmParams(2, 128, L.LBM_FP64, 0, 0.8, 0.0, 1.0, 1.0, 1.0)
+    assert lib.lbm_state_bytes(ctypes.byref(bad)) == 0
+    ctx = ctypes.c_void_p()
+    # rejected before any device work: too small, tau <= 0.5, NULL buffers, size mismatch
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(bad), ctypes.c_void_p(8), ctypes.c_void_p(16),
+                          0, None) == L.LBM_ERR_INVALID
+    badtau = L.LbmParams(64, 128, L.LBM_FP64, 0, 0.5, 0.0, 1.0, 1.0, 1.0)
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(badtau), ctypes.c_void_p(8), ctypes.c_void_p(16),
+                          37 * 134 * 64 * 8, None) == L.LBM_ERR_INVALID
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(p), None, None, 0, None) == L.LBM_ERR_INVALID
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(p), ctypes.c_void_p(8), ctypes.c_void_p(16),
+                          12345, None) == L.LBM_ERR_SIZE
+    assert not ctx.value
+    assert lib.lbm_step(None, 1) == L.LBM_ERR_INVALID

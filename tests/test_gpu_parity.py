@@ -1,0 +1,175 @@
+"""GPU parity of the fused D2Q37 step against the float64 oracle.
+
+Tolerances:
+* propagate + bc (pure moves, fixed-order wall sums, one product): bit-exact;
+* float64 full step: max |gpu - oracle| per population plane <= 1e-12 times
+  the plane's max |oracle| (the kernels evaluate the same polynomial with a
+  different association and FMA, so rounding differs at ~1e-16 per step);
+* float32 shifted storage: <= 2e-6 relative after 1 step, checked against
+  the float64 oracle (float32 rounding of the stored deviations).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lattice, model as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1703_00186_gb300.lbm import Lattice
+
+K = lattice.constants()
+
+
+def to_dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def encode32(f, rho0):
+    return (f - K["w"][:, None, None] * rho0).astype(np.float32)
+
+
+def decode32(d, rho0):
+    return d.astype(np.float64) + K["w"][:, None, None] * rho0
+
+
+def noisy_state(lx, ly, seed, eps=0.02, umax=0.1):
+    rho, ux, uy, T = synth.random_fields(lx, ly, seed, umax=umax)
+    f = M.init_state(rho, ux, uy, T)
+    f[:, 3:-3] *= 1.0 + eps * synth.noise(lx, ly, seed + 1)
+    return f
+
+
+def plane_err(a, b):
+    a, b = M.physical(a), M.physical(b)
+    scale = np.abs(b).max(axis=(1, 2))
+    return (np.abs(a - b).max(axis=(1, 2)) / scale).max()
+
+
+def make(p: M.Params, precision="fp64", rho0=1.0):
+    return Lattice(p.lx, p.ly, tau=p.tau, g=p.g, t_top=p.t_top, t_bottom=p.t_bottom,
+                   precision=precision, rho0=rho0, periodic_y=p.periodic_y)
+
+
+def test_library_constants_are_bit_identical_to_oracle():
+    p = M.Params(16, 12, tau=0.8, t_top=0.5, t_bottom=1.5)
+    lat = make(p)
+    r, w, qb, qt = lat.constants()
+    assert r == K["r"]
+    np.testing.assert_array_equal(w, K["w"])
+    np.testing.assert_array_equal(qb, M.wall_q(1.5, "bottom"))
+    np.testing.assert_array_equal(qt, M.wall_q(0.5, "top"))
+
+
+@pytest.mark.parametrize("lx,ly", [(64, 128), (67, 45), (3, 6), (130, 9)])
+@pytest.mark.parametrize("periodic_y", [False, True])
+def test_propagate_bc_is_bit_exact(lx, ly, periodic_y):
+    p = M.Params(lx, ly, tau=0.8, g=1e-4, t_top=0.7, t_bottom=1.3, periodic_y=periodic_y)
+    f = noisy_state(lx, ly, 100 + lx + ly, eps=0.3)
+    f[:, :3] = np.nan          # halos are never read as data
+    f[:, -3:] = np.nan
+    want = M.propagate_bc(f, p)
+    lat = make(p)
+    got = lat.propagate_bc(to_dev(f)).cpu().numpy()
+    np.testing.assert_array_equal(M.physical(got), M.physical(want))
+
+
+def test_init_matches_oracle_equilibrium():
+    lx, ly = 40, 24
+    rho, ux, uy, T = synth.random_fields(lx, ly, 7)
+    p = M.Params(lx, ly, tau=0.8)
+    lat = make(p)
+    lat.init(rho, ux, uy, T)
+    got = lat.state().cpu().numpy()
+    assert plane_err(got, M.init_state(rho, ux, uy, T)) < 1e-14
+
+
+@pytest.mark.parametrize("lx,ly", [(64, 128), (67, 45), (3, 6)])
+@pytest.mark.parametrize("periodic_y", [False, True])
+def test_one_step_parity_fp64(lx, ly, periodic_y):
+    p = M.Params(lx, ly, tau=0.7, g=2e-3, t_top=0.8, t_bottom=1.2, periodic_y=periodic_y)
+    f = noisy_state(lx, ly, 200 + lx, eps=0.05)
+    want = M.step(f, p)
+    lat = make(p)
+    lat.set_state(to_dev(f))
+    lat.step(1)
+    got = lat.state().cpu().numpy()
+    assert np.isnan(got[:, :3]).all() and np.isnan(got[:, -3:]).all()  # halos untouched
+    assert plane_err(got, want) <= 1e-12
+
+
+def test_rayleigh_taylor_64x128_100_steps_fp64():
+    # 64 x 128, 4 interface modes, tau = 0.8, g = 1e-4, 100 steps
+    rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 0)
+    p = M.Params(64, 128, tau=0.8, g=1e-4, t_top=tt, t_bottom=tb)
+    f0 = M.init_state(rho, ux, uy, T)
+    lat = make(p)
+    lat.init(rho, ux, uy, T)
+    g1 = lat.state().cpu().numpy()
+    assert plane_err(g1, f0) < 1e-14
+    lat.set_state(to_dev(f0))
+    want = f0
+    for n in (1, 99):
+        lat.step(n)
+        want = M.run(want, p, n)
+        got = lat.state().cpu().numpy()
+        assert plane_err(got, want) <= 1e-12, n
+    fields = [t.cpu().numpy() for t in lat.moments()]
+    ref = M.moments(M.physical(want))
+    for g, r in zip(fields, ref):
+        assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max() + 1e-15
+
+
+def test_moments_match_eq2():
+    lx, ly = 33, 20
+    f = noisy_state(lx, ly, 9)
+    p = M.Params(lx, ly, tau=0.8)
+    lat = make(p)
+    got = [t.cpu().numpy() for t in lat.moments(to_dev(f))]
+    ref = M.moments(M.physical(f))
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= 1e-13 * np.abs(r).max() + 1e-16
+
+
+def test_fp32_shifted_one_step_and_moments():
+    lx, ly = 64, 40
+    rho0 = 1.1
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.8, t_bottom=1.2)
+    f = noisy_state(lx, ly, 300, eps=0.02)
+    d = encode32(f, rho0)
+    fin = decode32(d, rho0)          # the exact input the fp32 path sees
+    want = M.step(fin, p)
+    lat = make(p, precision="fp32", rho0=rho0)
+    lat.set_state(to_dev(d, torch.float32))
+    lat.step(1)
+    got = decode32(lat.state().cpu().numpy(), rho0)
+    assert plane_err(got, want) <= 2e-6
+    fields = [t.cpu().numpy() for t in lat.moments()]
+    ref = M.moments(M.physical(decode32(encode32(want, rho0), rho0)))
+    for g, r in zip(fields, ref):
+        assert np.abs(g - r).max() <= 1e-6 * np.abs(r).max() + 1e-9
+
+
+def test_fp32_propagate_bc_moves_bits():
+    # Slots away from the walls are pure moves of the stored float32 bits.
+    lx, ly = 40, 20
+    p = M.Params(lx, ly, tau=0.7, t_top=0.8, t_bottom=1.2)
+    d = encode32(noisy_state(lx, ly, 301), 1.0)
+    lat = make(p, precision="fp32", rho0=1.0)
+    got = lat.propagate_bc(to_dev(d, torch.float32)).cpu().numpy()
+    want = M.propagate(d.astype(np.float64), p).astype(np.float32)
+    np.testing.assert_array_equal(M.physical(got)[:, 3:ly - 3], M.physical(want)[:, 3:ly - 3])
+
+
+def test_check_finite_and_status():
+    p = M.Params(16, 12, tau=0.8)
+    lat = make(p)
+    f = noisy_state(16, 12, 5)
+    lat.set_state(to_dev(f))
+    assert lat.check_finite()
+    f[4, 7, 3] = np.inf
+    lat.set_state(to_dev(f))
+    assert not lat.check_finite()
+    assert lat.status() == 0
