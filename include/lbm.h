@@ -122,6 +122,11 @@ int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux,
  * other; the buffers then swap roles. */
 int lbm_step(lbm_ctx* ctx, int n);
 
+/* One time step from state src into state dst (caller buffers in the
+ * context's precision, must not alias), leaving the context's own buffers and
+ * current state untouched.  Used to recompute checkpointed trajectories. */
+int lbm_step_from(lbm_ctx* ctx, const void* src, void* dst);
+
 /* Device pointer of the buffer holding the current state. */
 void* lbm_current(const lbm_ctx* ctx);
 

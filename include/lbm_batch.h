@@ -1,0 +1,90 @@
+/*
+ * lbm_batch.h - many independent D2Q37 lattices stepped together.
+ *
+ * A batch holds lattices of uneven sizes and parameters (each with its own
+ * walls, tau, g and FP32 shift) that share one precision.  One time step of
+ * the whole batch is one kernel launch whose blocks walk a single work list
+ * of tiles spanning every lattice (each tile runs the fused propagate, bc and
+ * collide of Sect. 2 / eq. 1 on its lattice); n steps are captured once into
+ * a CUDA graph and replayed with one graph launch.  The tile shape is chosen
+ * by lbm_batch_autotune, which times every candidate shape on the batch
+ * itself.  The paper has no batched mode; the per-lattice step is the one of
+ * include/lbm.h (same readings, layout and population order).
+ *
+ * OWNERSHIP.  The caller owns every lattice buffer (two per lattice, in the
+ * state layout of include/lbm.h) and the stream.  The batch allocates its
+ * own small device tables (lattice parameters and tile offsets) and its CUDA
+ * graphs; lbm_batch_destroy releases them.
+ *
+ * ERRORS.  As in include/lbm.h: LBM_OK or a negative LBM_ERR_* code, with a
+ * message from lbm_batch_last_error().
+ */
+#ifndef LBM_BATCH_H
+#define LBM_BATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_lattice_desc {
+  int32_t lx, ly;        /* lx >= 3, ly >= 6                                   */
+  double tau;            /* > 0.5                                              */
+  double g;              /* gravity magnitude along -y                         */
+  double t_top, t_bottom;
+  double rho0;           /* FP32 shift density                                 */
+  void* f_a;             /* current state after creation                       */
+  void* f_b;             /* second buffer; both lbm_state_bytes() bytes        */
+} lbm_lattice_desc;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Number of tile shapes lbm_batch_autotune chooses from, and the shape of
+ * candidate `i` (threads along x and y of a block; one site per thread). */
+int lbm_batch_tile_count(void);
+int lbm_batch_tile_shape(int i, int* bx, int* by);
+
+/* Create a batch of n >= 1 lattices in `precision` (LBM_FP64 or
+ * LBM_FP32_SHIFTED).  descs is a host array of n entries.  stream: cudaStream_t. */
+int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int precision,
+                     void* stream);
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Lattice i := f^eq(rho, u, T) (device fields [ly_i][lx_i]). */
+int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy,
+                   const double* T);
+
+/* Select tile shape `tile` (0 .. lbm_batch_tile_count()-1). */
+int lbm_batch_set_tile(lbm_batch* b, int tile);
+
+/* Time every tile shape over `steps` batch steps each (after one untimed
+ * step), keep the fastest and return its index in *best (and, if times_ms is
+ * not NULL, each candidate's time per step in times_ms[]).  The lattices
+ * advance by (steps + 1) x lbm_batch_tile_count() steps: re-initialise
+ * afterwards.  Synchronises the stream. */
+int lbm_batch_autotune(lbm_batch* b, int steps, int* best, double* times_ms);
+
+/* Advance every lattice by n >= 0 steps with one CUDA graph launch (the graph
+ * of n steps is captured on first use and cached). */
+int lbm_batch_step(lbm_batch* b, int n);
+
+/* Device pointer of the buffer holding lattice i's current state. */
+void* lbm_batch_current(const lbm_batch* b, int i);
+
+/* eq. (2) fields of lattice i's current state (device [ly_i][lx_i]). */
+int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy, double* T);
+
+/* Total physical sites of the batch (sum of lx_i * ly_i). */
+long long lbm_batch_sites(const lbm_batch* b);
+
+/* Synchronise and report the first asynchronous error. */
+int lbm_batch_status(lbm_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_BATCH_H */

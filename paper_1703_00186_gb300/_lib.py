@@ -52,6 +52,7 @@ SIGNATURES = {
     "lbm_set_stream": (c_int, [c_void_p, c_void_p]),
     "lbm_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_step": (c_int, [c_void_p, c_int]),
+    "lbm_step_from": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_current": (c_void_p, [c_void_p]),
     "lbm_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_get_state": (c_int, [c_void_p, c_void_p]),
@@ -64,6 +65,19 @@ SIGNATURES = {
     "lbm_status": (c_int, [c_void_p]),
     "lbm_constants": (c_int, [c_void_p, P(c_double), P(c_double), P(c_double), P(c_double)]),
     "lbm_probe_fma": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
+    "lbm_batch_tile_count": (c_int, []),
+    "lbm_batch_tile_shape": (c_int, [c_int, P(c_int), P(c_int)]),
+    "lbm_batch_create": (c_int, [P(c_void_p), c_int, P(LbmLatticeDesc), c_int, c_void_p]),
+    "lbm_batch_destroy": (None, [c_void_p]),
+    "lbm_batch_last_error": (c_char_p, [c_void_p]),
+    "lbm_batch_init": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_batch_set_tile": (c_int, [c_void_p, c_int]),
+    "lbm_batch_autotune": (c_int, [c_void_p, c_int, P(c_int), P(c_double)]),
+    "lbm_batch_step": (c_int, [c_void_p, c_int]),
+    "lbm_batch_current": (c_void_p, [c_void_p, c_int]),
+    "lbm_batch_moments": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_batch_sites": (ctypes.c_longlong, [c_void_p]),
+    "lbm_batch_status": (c_int, [c_void_p]),
 }
 
 _lib = None

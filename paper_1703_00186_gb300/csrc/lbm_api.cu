@@ -220,6 +220,12 @@ int lbm_step(lbm_ctx* c, int n) {
   return LBM_OK;
 }
 
+int lbm_step_from(lbm_ctx* c, const void* src, void* dst) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!src || !dst || src == dst) return fail(c, LBM_ERR_INVALID, "lbm_step_from: bad buffers");
+  return cuda_check(c, launch_step(c->p.precision, true, src, dst, c->args, c->stream), "lbm_step_from");
+}
+
 void* lbm_current(const lbm_ctx* c) { return c ? c->buf[c->cur] : nullptr; }
 
 int lbm_moments(lbm_ctx* c, const void* f, double* rho, double* ux, double* uy, double* T) {

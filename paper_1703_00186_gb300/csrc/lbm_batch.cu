@@ -1,0 +1,388 @@
+// Batched stepping of many independent D2Q37 lattices (include/lbm_batch.h).
+//
+// One launch advances every lattice of the batch by one step: block b finds
+// its lattice by a binary search of the tile offsets, copies that lattice's
+// constants into shared memory and runs the fused propagate + bc + collide
+// on its tile (the same device code as the single-lattice kernel).  n steps
+// are captured into a CUDA graph on a private stream and replayed on the
+// caller's stream.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lbm_batch.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t errlen);
+size_t element_size(int precision);
+cudaError_t launch_init(int prec, void* dst, const double* rho, const double* ux, const double* uy,
+                        const double* T, const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_moments(int prec, const void* src, double* rho, double* ux, double* uy, double* T,
+                           const LatticeArgs& a, cudaStream_t s);
+
+struct BatchEntry {
+  LatticeArgs a;
+  void* f[2];
+};
+
+namespace {
+
+constexpr int kTiles = 6;
+constexpr int kTileBX[kTiles] = {32, 32, 64, 128, 32, 64};
+constexpr int kTileBY[kTiles] = {4, 8, 2, 1, 2, 4};
+
+template <int PREC>
+struct BCodec;
+template <>
+struct BCodec<LBM_FP64> {
+  using T = double;
+  const LatticeArgs* a;
+  __device__ double operator()(int, double v) const { return v; }
+  __device__ double enc(int, double v) const { return v; }
+};
+template <>
+struct BCodec<LBM_FP32_SHIFTED> {
+  using T = float;
+  const LatticeArgs* a;
+  __device__ double operator()(int l, float v) const { return a->w_rho0[l] + (double)v; }
+  __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
+};
+
+template <int PREC, int TBX, int TBY>
+__global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry* __restrict__ ent,
+                                                               const long long* __restrict__ tile_start,
+                                                               int n, int parity) {
+  using T = typename BCodec<PREC>::T;
+  __shared__ __align__(16) LatticeArgs sa;
+  __shared__ const void* s_src;
+  __shared__ void* s_dst;
+  const long long b = blockIdx.x;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(tile_start + mid) <= b) lo = mid; else hi = mid - 1;
+  }
+  const int tid = threadIdx.y * TBX + threadIdx.x;
+  {
+    static_assert(sizeof(LatticeArgs) % 8 == 0, "LatticeArgs must be a multiple of 8 bytes");
+    const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&ent[lo].a);
+    unsigned long long* s = reinterpret_cast<unsigned long long*>(&sa);
+    for (int k = tid; k < (int)(sizeof(LatticeArgs) / 8); k += TBX * TBY) s[k] = __ldg(g + k);
+    if (tid == 0) {
+      s_src = ent[lo].f[parity];
+      s_dst = ent[lo].f[parity ^ 1];
+    }
+  }
+  __syncthreads();
+  const LatticeArgs& a = sa;
+  const long long t = b - __ldg(tile_start + lo);
+  const int tiles_x = (a.lx + TBX - 1) / TBX;
+  const int ty = (int)(t / tiles_x), tx = (int)(t - (long long)ty * tiles_x);
+  const int x = tx * TBX + threadIdx.x;
+  const int y = ty * TBY + threadIdx.y;
+  if (x >= a.lx || y >= a.ly) return;
+  const T* __restrict__ src = static_cast<const T*>(s_src);
+  T* __restrict__ dst = static_cast<T*>(s_dst);
+  BCodec<PREC> codec{&a};
+  T f[NPOP];
+  pull(src, x, y, a, f);
+  walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+  if constexpr (PREC == LBM_FP64)
+    collide_fp64(f, a);
+  else
+    collide_fp32(f, a);
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
+}
+
+template <int PREC, int I>
+cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long long* ts, int n, int parity,
+                          cudaStream_t s) {
+  constexpr int BX = kTileBX[I], BY = kTileBY[I];
+  batch_step_kernel<PREC, BX, BY><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, n, parity);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_tile(int tile, long long blocks, const BatchEntry* ent, const long long* ts, int n, int parity,
+                        cudaStream_t s) {
+  switch (tile) {
+    case 0: return launch_tile_i<PREC, 0>(blocks, ent, ts, n, parity, s);
+    case 1: return launch_tile_i<PREC, 1>(blocks, ent, ts, n, parity, s);
+    case 2: return launch_tile_i<PREC, 2>(blocks, ent, ts, n, parity, s);
+    case 3: return launch_tile_i<PREC, 3>(blocks, ent, ts, n, parity, s);
+    case 4: return launch_tile_i<PREC, 4>(blocks, ent, ts, n, parity, s);
+    default: return launch_tile_i<PREC, 5>(blocks, ent, ts, n, parity, s);
+  }
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+  int n;
+  int precision;
+  cudaStream_t stream;
+  cudaStream_t capture;
+  std::vector<LatticeArgs> args;
+  std::vector<void*> fa, fb;
+  BatchEntry* d_ent;
+  long long* d_tiles[kTiles];  // tile offsets per shape
+  long long blocks[kTiles];
+  int tile;
+  int parity;
+  long long sites;
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (n, parity, tile)
+  char err[512];
+};
+
+namespace {
+
+int bfail(lbm_batch* b, int code, const char* fmt, ...) {
+  if (b) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(b->err, sizeof b->err, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int bcuda(lbm_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LBM_OK;
+  return bfail(b, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaError_t launch_batch(const lbm_batch* b, int parity, cudaStream_t s) {
+  const int t = b->tile;
+  if (b->precision == LBM_FP64)
+    return launch_tile<LBM_FP64>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
+  return launch_tile<LBM_FP32_SHIFTED>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
+}
+
+void free_batch(lbm_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  for (int t = 0; t < kTiles; ++t)
+    if (b->d_tiles[t]) cudaFree(b->d_tiles[t]);
+  if (b->d_ent) cudaFree(b->d_ent);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
+
+// Graph of n batch steps starting at parity p with the current tile shape.
+int get_graph(lbm_batch* b, int n, cudaGraphExec_t* out) {
+  auto key = std::make_tuple(n, b->parity, b->tile);
+  auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return LBM_OK;
+  }
+  cudaGraph_t g = nullptr;
+  int rc = bcuda(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "graph capture");
+  if (rc) return rc;
+  cudaError_t le = cudaSuccess;
+  int p = b->parity;
+  for (int i = 0; i < n && le == cudaSuccess; ++i) {
+    le = launch_batch(b, p, b->capture);
+    p ^= 1;
+  }
+  cudaError_t ee = cudaStreamEndCapture(b->capture, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bcuda(b, le, "batch launch during capture");
+  }
+  rc = bcuda(b, ee, "graph end capture");
+  if (rc) return rc;
+  cudaGraphExec_t exec = nullptr;
+  rc = bcuda(b, cudaGraphInstantiate(&exec, g, 0), "graph instantiate");
+  cudaGraphDestroy(g);
+  if (rc) return rc;
+  b->graphs[key] = exec;
+  *out = exec;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_tile_count(void) { return kTiles; }
+
+int lbm_batch_tile_shape(int i, int* bx, int* by) {
+  if (i < 0 || i >= kTiles || !bx || !by) return LBM_ERR_INVALID;
+  *bx = kTileBX[i];
+  *by = kTileBY[i];
+  return LBM_OK;
+}
+
+int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int precision, void* stream) {
+  if (!out) return LBM_ERR_INVALID;
+  *out = nullptr;
+  if (n < 1 || !descs) return LBM_ERR_INVALID;
+  if (precision != LBM_FP64 && precision != LBM_FP32_SHIFTED) return LBM_ERR_INVALID;
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ERR_INVALID;
+  b->n = n;
+  b->precision = precision;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->args.resize(n);
+  b->fa.resize(n);
+  b->fb.resize(n);
+  b->sites = 0;
+  for (int i = 0; i < n; ++i) {
+    const lbm_lattice_desc& d = descs[i];
+    lbm_params p{d.lx, d.ly, precision, 0, d.tau, d.g, d.t_top, d.t_bottom, d.rho0};
+    int rc = make_lattice_args(p, &b->args[i], b->err, sizeof b->err);
+    if (rc != LBM_OK || !d.f_a || !d.f_b || d.f_a == d.f_b) {
+      free_batch(b);
+      return rc != LBM_OK ? rc : LBM_ERR_INVALID;
+    }
+    b->fa[i] = d.f_a;
+    b->fb[i] = d.f_b;
+    b->sites += (long long)d.lx * d.ly;
+  }
+  std::vector<BatchEntry> h(n);
+  for (int i = 0; i < n; ++i) {
+    h[i].a = b->args[i];
+    h[i].f[0] = b->fa[i];
+    h[i].f[1] = b->fb[i];
+  }
+  if (cudaMalloc(&b->d_ent, sizeof(BatchEntry) * n) != cudaSuccess ||
+      cudaMemcpy(b->d_ent, h.data(), sizeof(BatchEntry) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return LBM_ERR_CUDA;
+  }
+  for (int t = 0; t < kTiles; ++t) {
+    std::vector<long long> ts(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      const long long tiles = (long long)((b->args[i].lx + kTileBX[t] - 1) / kTileBX[t]) *
+                              ((b->args[i].ly + kTileBY[t] - 1) / kTileBY[t]);
+      ts[i + 1] = ts[i] + tiles;
+    }
+    b->blocks[t] = ts[n];
+    if (ts[n] >= (1LL << 31) || cudaMalloc(&b->d_tiles[t], sizeof(long long) * (n + 1)) != cudaSuccess ||
+        cudaMemcpy(b->d_tiles[t], ts.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return LBM_ERR_CUDA;
+    }
+  }
+  if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return LBM_ERR_CUDA;
+  }
+  b->tile = 0;
+  b->parity = 0;
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }
+
+int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy, const double* T) {
+  if (!b) return LBM_ERR_INVALID;
+  if (i < 0 || i >= b->n || !rho || !ux || !uy || !T) return bfail(b, LBM_ERR_INVALID, "lbm_batch_init: bad args");
+  void* cur = b->parity ? b->fb[i] : b->fa[i];
+  return bcuda(b, launch_init(b->precision, cur, rho, ux, uy, T, b->args[i], b->stream), "lbm_batch_init");
+}
+
+int lbm_batch_set_tile(lbm_batch* b, int tile) {
+  if (!b) return LBM_ERR_INVALID;
+  if (tile < 0 || tile >= kTiles) return bfail(b, LBM_ERR_INVALID, "tile %d out of range", tile);
+  b->tile = tile;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+  if (!b) return LBM_ERR_INVALID;
+  if (n < 0) return bfail(b, LBM_ERR_INVALID, "lbm_batch_step: n < 0");
+  if (n == 0) return LBM_OK;
+  cudaGraphExec_t exec;
+  int rc = get_graph(b, n, &exec);
+  if (rc) return rc;
+  rc = bcuda(b, cudaGraphLaunch(exec, b->stream), "graph launch");
+  if (rc) return rc;
+  b->parity ^= (n & 1);
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int steps, int* best, double* times_ms) {
+  if (!b) return LBM_ERR_INVALID;
+  if (steps < 1 || !best) return bfail(b, LBM_ERR_INVALID, "lbm_batch_autotune: bad args");
+  cudaEvent_t e0, e1;
+  int rc = bcuda(b, cudaEventCreate(&e0), "event");
+  if (rc) return rc;
+  rc = bcuda(b, cudaEventCreate(&e1), "event");
+  if (rc) {
+    cudaEventDestroy(e0);
+    return rc;
+  }
+  double best_t = 1e300;
+  int best_i = 0;
+  for (int t = 0; t < kTiles && rc == LBM_OK; ++t) {
+    b->tile = t;
+    rc = lbm_batch_step(b, 1);  // warm-up (and graph capture of the 1-step graph)
+    cudaGraphExec_t exec;
+    if (!rc) rc = get_graph(b, steps, &exec);
+    if (!rc) rc = bcuda(b, cudaEventRecord(e0, b->stream), "event record");
+    if (!rc) rc = lbm_batch_step(b, steps);
+    if (!rc) rc = bcuda(b, cudaEventRecord(e1, b->stream), "event record");
+    if (!rc) rc = bcuda(b, cudaEventSynchronize(e1), "event sync");
+    float ms = 0.f;
+    if (!rc) rc = bcuda(b, cudaEventElapsedTime(&ms, e0, e1), "event time");
+    if (!rc) {
+      const double per = ms / steps;
+      if (times_ms) times_ms[t] = per;
+      if (per < best_t) {
+        best_t = per;
+        best_i = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->tile = best_i;
+  *best = best_i;
+  return LBM_OK;
+}
+
+void* lbm_batch_current(const lbm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->parity ? b->fb[i] : b->fa[i];
+}
+
+int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy, double* T) {
+  if (!b) return LBM_ERR_INVALID;
+  if (i < 0 || i >= b->n) return bfail(b, LBM_ERR_INVALID, "lbm_batch_moments: bad index");
+  return bcuda(b, launch_moments(b->precision, lbm_batch_current(b, i), rho, ux, uy, T, b->args[i], b->stream),
+               "lbm_batch_moments");
+}
+
+long long lbm_batch_sites(const lbm_batch* b) { return b ? b->sites : 0; }
+
+int lbm_batch_status(lbm_batch* b) {
+  if (!b) return LBM_ERR_INVALID;
+  return bcuda(b, cudaStreamSynchronize(b->stream), "lbm_batch_status");
+}
+
+}  // extern "C"

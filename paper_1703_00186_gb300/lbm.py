@@ -111,6 +111,11 @@ class Lattice:
         self._check(self.lib.lbm_step(self.ctx, int(n)))
         return self
 
+    def step_from(self, src: torch.Tensor, dst: torch.Tensor):
+        """One step from state src into state dst (context buffers untouched)."""
+        self._check(self.lib.lbm_step_from(self.ctx, _ptr(src), _ptr(dst)))
+        return dst
+
     def state(self) -> torch.Tensor:
         """The buffer holding the current state (a view; it changes role at each step)."""
         ptr = self.lib.lbm_current(self.ctx)

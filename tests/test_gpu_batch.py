@@ -1,0 +1,115 @@
+"""GPU parity of the batched, graph-captured multi-lattice step.
+
+Every lattice of a batch of uneven sizes and parameters must evolve exactly
+as the oracle evolves it alone (float64: <= 1e-12 per population plane;
+float32 shifted storage: <= 2e-6 after one step), for every tile shape, and
+the autotuner must leave a valid tile shape selected.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lattice, model as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1703_00186_gb300.batch import Batch
+
+K = lattice.constants()
+
+SPECS = [
+    dict(lx=40, ly=24, tau=0.8, g=1e-3, delta=0.4),
+    dict(lx=67, ly=45, tau=0.6, g=1e-4, delta=0.2),
+    dict(lx=32, ly=6, tau=0.9, g=0.0, delta=0.6),
+    dict(lx=100, ly=30, tau=0.7, g=5e-4, delta=0.3),
+    dict(lx=3, ly=9, tau=1.0, g=2e-3, delta=0.5),
+]
+
+
+def fields(i, s):
+    rho, ux, uy, T, tt, tb = synth.rt_fields(s["lx"], s["ly"], 2, 10 + i, delta=s["delta"], width=1.5)
+    return (rho, ux, uy, T), tt, tb
+
+
+def build(precision):
+    specs = []
+    flds = []
+    for i, s in enumerate(SPECS):
+        f, tt, tb = fields(i, s)
+        specs.append(dict(lx=s["lx"], ly=s["ly"], tau=s["tau"], g=s["g"], t_top=tt, t_bottom=tb,
+                          rho0=float(f[0].mean())))
+        flds.append(f)
+    return specs, flds
+
+
+def plane_err(a, b):
+    a, b = M.physical(a), M.physical(b)
+    scale = np.abs(b).max(axis=(1, 2))
+    return (np.abs(a - b).max(axis=(1, 2)) / scale).max()
+
+
+def oracle_run(spec, f, n):
+    p = M.Params(spec["lx"], spec["ly"], tau=spec["tau"], g=spec["g"], t_top=spec["t_top"],
+                 t_bottom=spec["t_bottom"])
+    return M.run(M.init_state(*f), p, n)
+
+
+@pytest.mark.parametrize("tile", range(6))
+def test_batch_fp64_matches_oracle_for_every_tile_shape(tile):
+    specs, flds = build("fp64")
+    b = Batch(specs, precision="fp64")
+    b.set_tile(tile)
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    n = 5
+    b.step(2).step(3)   # two graph launches (cached graphs of 2 and 3 steps)
+    for i, (s, f) in enumerate(zip(specs, flds)):
+        got = b.state(i).cpu().numpy()
+        assert plane_err(got, oracle_run(s, f, n)) <= 1e-12, i
+    assert b.status() == 0
+
+
+def test_batch_fp32_one_step_matches_oracle():
+    specs, flds = build("fp32")
+    b = Batch(specs, precision="fp32")
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    b.step(1)
+    for i, (s, f) in enumerate(zip(specs, flds)):
+        rho0 = s["rho0"]
+        d0 = (M.init_state(*f) - K["w"][:, None, None] * rho0).astype(np.float32)
+        fin = d0.astype(np.float64) + K["w"][:, None, None] * rho0
+        p = M.Params(s["lx"], s["ly"], tau=s["tau"], g=s["g"], t_top=s["t_top"], t_bottom=s["t_bottom"])
+        want = M.step(fin, p)
+        got = b.state(i).cpu().numpy().astype(np.float64) + K["w"][:, None, None] * rho0
+        assert plane_err(got, want) <= 2e-6, i
+
+
+def test_autotune_selects_a_valid_shape_and_results_stay_exact():
+    specs, flds = build("fp64")
+    b = Batch(specs, precision="fp64")
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    best, times = b.autotune(steps=2)
+    assert 0 <= best < len(Batch.tile_shapes())
+    assert all(t > 0 for t in times) and times[best] == min(times)
+    for i, f in enumerate(flds):   # the tuner advanced the lattices: start again
+        b.init(i, *f)
+    b.step(4)
+    for i, (s, f) in enumerate(zip(specs, flds)):
+        assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, f, 4)) <= 1e-12
+
+
+def test_batch_moments():
+    specs, flds = build("fp64")
+    b = Batch(specs, precision="fp64")
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    b.step(3)
+    for i, (s, f) in enumerate(zip(specs, flds)):
+        want = M.moments(M.physical(oracle_run(s, f, 3)))
+        got = [t.cpu().numpy() for t in b.moments(i)]
+        for g, w in zip(got, want):
+            assert np.abs(g - w).max() <= 1e-12 * np.abs(w).max() + 1e-15
