@@ -157,6 +157,43 @@ int lbm_propagate_bc(lbm_ctx* ctx, const void* src, void* dst);
 int lbm_adjoint_step(lbm_ctx* ctx, const void* f_t, const double* lam_in,
                      double* lam_out);
 
+/* The adjoint step without a context and without any device allocation.
+ * The paper has no counterpart of this call.
+ *
+ * Who needs it: lbm_create allocates a small device block, so a caller that
+ * cannot call cudaMalloc cannot create a context.  Such callers include a
+ * host application whose device memory is all handed out by another allocator
+ * (for example a framework's caching allocator that reserved the GPU up
+ * front), and code that must not allocate after its set-up phase because
+ * cudaMalloc can synchronise the device.  This call computes what
+ * lbm_adjoint_step computes for a context with parameters *p.
+ *
+ * Arguments: f_t, lam_in and lam_out as for lbm_adjoint_step (caller-owned
+ * device buffers, must not alias); stream is a cudaStream_t (NULL = legacy
+ * default stream).  The lattice constants are derived on the host at every
+ * call.
+ *
+ * Scratch: the per-wall-row sums that lbm_adjoint_step keeps in the halo rows
+ * of lam_out go instead to one fixed array inside the library of
+ * 6 x LBM_NOALLOC_MAX_LX doubles (768 KiB).  Every GPU that loads the library
+ * holds this array until the process exits.  The halo rows of lam_out are
+ * left untouched.
+ *
+ * Set-up: the first call on a device looks up the array's device address,
+ * with that device current; make that first call before any stream capture.
+ *
+ * Sharing: every call shares the array, and the array keeps the last call's
+ * contents.  Each call overwrites every entry it reads, so nothing needs
+ * clearing.  Calls that overlap on the GPU (other streams, other host threads)
+ * race and give wrong results; calls ordered on one stream are safe.
+ *
+ * Returns LBM_OK; LBM_ERR_SIZE if p->lx > LBM_NOALLOC_MAX_LX (no work done);
+ * LBM_ERR_INVALID for bad parameters or pointers; LBM_ERR_CUDA if the address
+ * lookup or a launch fails. */
+#define LBM_NOALLOC_MAX_LX 16384
+int lbm_adjoint_step_noalloc(const lbm_params* p, const void* f_t,
+                             const double* lam_in, double* lam_out, void* stream);
+
 /* Vector-Jacobian product of lbm_moments at state f:
  *   lam_out_l = d rho/d f_l g_rho + d u/d f_l . g_u + d T/d f_l g_T
  * (eq. 2).  Cotangent fields [ly][lx]; any of them may be NULL (zero).

@@ -22,6 +22,7 @@ LBM_ERR_STATE = -6
 LBM_FP64 = 0
 LBM_FP32_SHIFTED = 1
 LBM_FLAG_PERIODIC_Y = 1
+LBM_NOALLOC_MAX_LX = 16384
 
 c_int = ctypes.c_int
 c_double = ctypes.c_double
@@ -59,6 +60,7 @@ SIGNATURES = {
     "lbm_set_state": (c_int, [c_void_p, c_void_p]),
     "lbm_propagate_bc": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_adjoint_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_adjoint_step_noalloc": (c_int, [P(LbmParams), c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_moments_vjp": (c_int, [c_void_p] * 7),
     "lbm_init_vjp": (c_int, [c_void_p] * 10),
     "lbm_check_finite": (c_int, [c_void_p, c_void_p, P(c_int)]),
