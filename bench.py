@@ -45,6 +45,7 @@ FP64_FLOP_PER_SITE = 547
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
+SECTIONS = ("fp64", "fp32", "adjoint", "e2e", "fp32_error", "rollout", "batch", "cpu")
 
 
 def parse():
@@ -55,8 +56,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lx", type=int, default=2048)
     ap.add_argument("--ly", type=int, default=4096)
-    ap.add_argument("--only", default="", help="comma list of sections: fp64,fp32,adjoint,e2e,cpu")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--only", default="", help="comma list of sections: " + ",".join(SECTIONS))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--error-steps", type=int, default=1000)
+    ap.add_argument("--rollout-steps", type=int, default=2000)
+    ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -166,13 +170,160 @@ def cpu_baseline(lx, ly, budget_s):
     f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
     steps = 2
     t0 = time.perf_counter()
+    c0 = time.process_time()
     for _ in range(steps):
         f = M.step(f, p)
     dt = time.perf_counter() - t0
+    cores = (time.process_time() - c0) / dt  # threads NumPy actually kept busy
     assert np.isfinite(M.physical(f)).all()
-    return {"value": width * ly * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    return {"value": width * ly * steps / dt / 1e6, "unit": "MLUPS", "cores": round(cores, 2),
+            "cores_available": len(os.sched_getaffinity(0)), "kind": "oracle",
             "sample": f"{width}x{ly} column slab of the 2048x4096 RT lattice (periodic in x), "
-                      f"{steps} steps, NumPy float64, single thread; {dt:.1f} s"}
+                      f"{steps} steps, NumPy float64; {dt:.1f} s"}
+
+
+def _field_errors(a, b):
+    """max |a - b| / max |b| for each of rho, ux, uy, T (b is the float64 run)."""
+    names = ("rho", "ux", "uy", "T")
+    out = {}
+    for n, x, y in zip(names, a, b):
+        d = (x - y).abs().max().item()
+        scale = y.abs().max().item()
+        out[n] = d / scale if scale > 0 else d
+    return out
+
+
+def fp32_error_study(lx, ly, steps, torch):
+    """Field error of the FP32-store path against the float64 path (which the
+    tests pin to the oracle within 1e-12), every 100 steps.  Two contrasts:
+    the workload's (T = 0.5 / 1.5, which the plain BGK model cannot keep
+    stable at tau = 0.6) and a stable one (T = 0.75 / 1.25)."""
+    import synth
+    from paper_1703_00186_gb300.lbm import Lattice
+    res = {}
+    for label, delta in (("delta_1.0", 1.0), ("delta_0.5", 0.5)):
+        rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 32, 0, delta=delta)
+        r0 = float(rho.mean())
+        a = Lattice(lx, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb, precision="fp64").init(rho, ux, uy, T)
+        b = Lattice(lx, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb, precision="fp32",
+                    rho0=r0).init(rho, ux, uy, T)
+        a.step(1)
+        b.step(1)
+        rows = [{"step": 1, **_field_errors(b.moments(), a.moments())}]
+        done = 1
+        while done < steps:
+            k = min(100 - done % 100, steps - done)
+            a.step(k)
+            b.step(k)
+            done += k
+            finite = a.check_finite() and b.check_finite()
+            row = {"step": done, "finite": finite}
+            if finite:
+                row.update(_field_errors(b.moments(), a.moments()))
+            rows.append(row)
+        res[label] = {"t_top": tt, "t_bottom": tb, "rho0": r0, "errors": rows}
+        del a, b
+        torch.cuda.empty_cache()
+    res["definition"] = ("max |fp32 - fp64| / max |fp64| per field on the 2048x4096 RT lattice, "
+                         "tau = 0.6, g = 1e-5, 32 modes")
+    return res
+
+
+def rollout_study(steps, torch):
+    """Checkpointed adjoint rollout on a 256 x 512 RT lattice: time of the
+    forward rollout and of the backward sweep (recompute + adjoint steps),
+    and the gradient against float64 central differences on 16 seeded
+    directions; FP64 and FP32-store."""
+    import numpy as np
+
+    import synth
+    from paper_1703_00186_gb300.adjoint import temperature_loss
+    from paper_1703_00186_gb300.lbm import Lattice
+    lx, ly, K, tau, g = 256, 512, 50, 0.8, 1e-4
+    rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 4, 1)
+    target = T + synth.smooth_field(lx, ly, 2, amp=0.05)
+    dT0 = 0.01 * synth.smooth_field(lx, ly, 3, amp=1.0)
+    dev = "cuda"
+    rho_t, T_t, tgt = (torch.tensor(v, device=dev) for v in (rho, T, target))
+    res = {"lattice": f"{lx}x{ly}", "steps": steps, "checkpoint_every": K, "tau": tau, "g": g}
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        lat = Lattice(lx, ly, tau=tau, g=g, t_top=tt, t_bottom=tb, precision=prec, rho0=float(rho.mean()))
+        d = torch.tensor(dT0, device=dev, requires_grad=True)
+        temperature_loss(d, lat, rho_t, T_t, tgt, 4, 2).backward()  # warm-up
+        d.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = temperature_loss(d, lat, rho_t, T_t, tgt, steps, K)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        grads[prec] = d.grad.detach().cpu().numpy()
+        res[prec] = {"J": float(J.detach()), "forward_s": t1 - t0, "backward_s": t2 - t1,
+                     "backward_over_forward": (t2 - t1) / (t1 - t0)}
+        if prec == "fp64":
+            rng = np.random.default_rng(2024)
+            eps = 1e-4
+            errs = []
+            for _ in range(16):
+                v = rng.standard_normal(dT0.shape)
+                with torch.no_grad():
+                    jp = float(temperature_loss(torch.tensor(dT0 + eps * v, device=dev), lat, rho_t, T_t, tgt,
+                                                steps, K))
+                    jm = float(temperature_loss(torch.tensor(dT0 - eps * v, device=dev), lat, rho_t, T_t, tgt,
+                                                steps, K))
+                fd = (jp - jm) / (2 * eps)
+                ad = float((grads["fp64"] * v).sum())
+                errs.append(abs(fd - ad) / abs(ad))
+            res["fp64"]["fd_max_rel_err_16_dirs"] = max(errs)
+            res["fp64"]["fd_eps"] = eps
+        del lat
+        torch.cuda.empty_cache()
+    g64, g32 = grads["fp64"], grads["fp32"]
+    res["fp32"]["grad_rel_diff_vs_fp64"] = float(np.abs(g32 - g64).max() / np.abs(g64).max())
+    return res
+
+
+def batch_study(steps, torch):
+    """64 independent RT lattices of uneven sizes and parameters, FP32-store,
+    autotuned tile, `steps` steps as one CUDA-graph launch."""
+    import synth
+    from paper_1703_00186_gb300.batch import Batch
+    specs = synth.batch_lattices(64, 7)
+    flds, descs = [], []
+    for sp in specs:
+        rho, ux, uy, T, tt, tb = synth.rt_fields(sp.lx, sp.ly, 8, sp.seed, delta=sp.delta)
+        flds.append((rho, ux, uy, T))
+        descs.append(dict(lx=sp.lx, ly=sp.ly, tau=sp.tau, g=sp.g, t_top=tt, t_bottom=tb, rho0=float(rho.mean())))
+    b = Batch(descs, precision="fp32")
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    best, times = b.autotune(steps=3)
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    b.step(steps)          # capture the graph once (untimed) ...
+    for i, f in enumerate(flds):
+        b.init(i, *f)      # ... and start again from the initial state
+    s = b.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    b.step(steps)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    finite = 0
+    for i in range(len(b)):
+        finite += int(bool(torch.isfinite(b.state(i)[:, 3:-3]).all()))
+    shapes = Batch.tile_shapes()
+    return {"lattices": len(b), "sites": b.sites, "steps": steps, "graph_launches": 1,
+            "kernel_launches": steps, "ms": ms, "mlups": b.sites * steps / (ms * 1e-3) / 1e6,
+            "tile": shapes[best], "autotune_ms_per_step": {f"{bx}x{by}": t for (bx, by), t in zip(shapes, times)},
+            "lattices_finite_after": finite,
+            "state_bytes": 2 * 37 * 4 * sum(sp.lx * (sp.ly + 6) for sp in specs)}
 
 
 def run_reference(args):
@@ -230,7 +381,7 @@ def main():
 
     from paper_1703_00186_gb300 import _lib as L
     lib = L.load()
-    only = set(filter(None, args.only.split(","))) or {"fp64", "fp32", "adjoint", "e2e", "cpu"}
+    only = set(filter(None, args.only.split(","))) or set(SECTIONS)
     lx, ly, K, W = args.lx, args.ly, args.steps, args.warmup
     sites = lx * ly
     out = {}
@@ -315,6 +466,15 @@ def main():
                       "h2d_bytes_per_step": lat.nbytes, "d2h_bytes_per_step": lat.nbytes,
                       "steps": ke, "path": "lbm_set_state(pinned host) + lbm_step(1) + lbm_get_state(pinned host)"}
         del lat, host_in, host_out
+    if "fp32_error" in only:
+        out["fp32_error"] = fp32_error_study(lx, ly, args.error_steps, torch)
+        torch.cuda.empty_cache()
+    if "rollout" in only:
+        out["rollout"] = rollout_study(args.rollout_steps, torch)
+        torch.cuda.empty_cache()
+    if "batch" in only:
+        out["batch"] = batch_study(args.batch_steps, torch)
+        torch.cuda.empty_cache()
     barrier(torch, world)
     if rank != 0:
         if world > 1:
@@ -355,6 +515,9 @@ def main():
         res["adjoint"] = out["adjoint"]
     if "e2e" in out:
         res["e2e"] = out["e2e"]
+    for key in ("fp32_error", "rollout", "batch"):
+        if key in out:
+            res[key] = out[key]
     res["fp64_probe_tflops"] = fp64_peak
     if "cpu" in only:
         res["cpu_baseline"] = cpu_baseline(lx, ly, args.cpu_seconds)

@@ -139,6 +139,68 @@ __device__ __forceinline__ Moments moment_sums(Get get) {
   return mo;
 }
 
+// Double-float accumulation (Knuth's TwoSum and the FMA exact product): a
+// sum is kept as hi + lo, where every addition into hi is error-free and the
+// rounding errors are collected in lo.  For sums of float32 values with small
+// integer weights this bounds the error by about 2 u^2 sum |x| (u = 2^-24),
+// the size of the rounding error of a float64 summation.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void f2_add(F2& acc, float x) {
+  const float s = acc.hi + x;
+  const float bb = s - acc.hi;
+  const float e = (acc.hi - (s - bb)) + (x - bb);
+  acc.hi = s;
+  acc.lo += e;
+}
+
+// acc += k x for a small integer k (k x rounded, its error added exactly).
+__device__ __forceinline__ void f2_add_mul(F2& acc, int k, float x) {
+  if (k == 1) {
+    f2_add(acc, x);
+  } else if (k == -1) {
+    f2_add(acc, -x);
+  } else if (k == 2 || k == -2 || k == 4 || k == 8) {
+    f2_add(acc, (float)k * x);  // power-of-two multiples are exact
+  } else {
+    const float p = (float)k * x;
+    const float e = fmaf((float)k, x, -p);
+    f2_add(acc, p);
+    acc.lo += e;
+  }
+}
+
+__device__ __forceinline__ double f2_to_double(const F2& a) { return (double)a.hi + (double)a.lo; }
+
+// Moment sums of 37 float32 values (rho, Jx, Jy, Exi as in moment_sums),
+// accumulated in double-float and returned as float64.
+__device__ __forceinline__ Moments moment_sums_f2(const float (&d)[NPOP]) {
+  F2 r{d[0], 0.f}, jx{0.f, 0.f}, jy{0.f, 0.f}, e{0.f, 0.f};
+  bool jx0 = true, jy0 = true, e0 = true;
+#pragma unroll
+  for (int l = 1; l < NPOP; ++l) {
+    f2_add(r, d[l]);
+    if (vx(l) != 0) {
+      if (jx0) { jx.hi = (float)vx(l) * d[l]; jx.lo = fmaf((float)vx(l), d[l], -jx.hi); jx0 = false; }
+      else f2_add_mul(jx, vx(l), d[l]);
+    }
+    if (vy(l) != 0) {
+      if (jy0) { jy.hi = (float)vy(l) * d[l]; jy.lo = fmaf((float)vy(l), d[l], -jy.hi); jy0 = false; }
+      else f2_add_mul(jy, vy(l), d[l]);
+    }
+    if (e0) { e.hi = (float)sq(l) * d[l]; e.lo = fmaf((float)sq(l), d[l], -e.hi); e0 = false; }
+    else f2_add_mul(e, sq(l), d[l]);
+  }
+  Moments mo;
+  mo.rho = f2_to_double(r);
+  mo.Jx = f2_to_double(jx);
+  mo.Jy = f2_to_double(jy);
+  mo.Exi = f2_to_double(e);
+  return mo;
+}
+
 // Site state derived from the moments: velocity in xi units and temperature.
 struct SiteFields {
   double rho, inv, ux, uy, T;  // u = r (ux, uy)
@@ -182,12 +244,14 @@ __device__ __forceinline__ void collide_fp64(double (&f)[NPOP], const LatticeArg
   }
 }
 
-// BGK collide on float32 deviations d_l = f_l - w_l rho0: the moment sums,
-// the velocity, the temperature and the temperature-dependent equilibrium
-// coefficients in float64; the per-population polynomial and relaxation in
-// float32:  d_l <- (1 - omega) d_l + omega (f^eq_l - w_l rho0).
+// BGK collide on float32 deviations d_l = f_l - w_l rho0.  The moment sums
+// are accumulated in double-float (float64-class error, on the FP32 pipe)
+// and handed over as float64; the velocity, the temperature and the
+// temperature-dependent equilibrium coefficients are float64; the
+// per-population polynomial and relaxation are float32:
+//   d_l <- (1 - omega) d_l + omega (f^eq_l - w_l rho0).
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
-  Moments mo = moment_sums([&](int l) { return (double)d[l]; });
+  Moments mo = moment_sums_f2(d);
   // add back the shift: sum w rho0 = rho0, sum w xi = 0, sum w |xi|^2 = D / r^2
   mo.rho += a.rho0;
   mo.Exi = fma(2.0 * a.inv_r2, a.rho0, mo.Exi);
