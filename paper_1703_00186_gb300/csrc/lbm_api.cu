@@ -95,6 +95,26 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     a->w_rho0[l] = q->w[l] * p.rho0;
     a->w_rho0_f[l] = (float)a->w_rho0[l];
   }
+  for (int j = 0; j < NSHELL; ++j) {
+    a->w_shell_f[j] = (float)q->w_shell[j];
+    a->c2_shell_f[j] = (float)q->c2_shell[j];
+  }
+  a->omega_f = (float)a->omega;
+  a->omc_f = (float)a->omc;
+  auto split = [](double v, float out[2]) {
+    out[0] = (float)v;
+    out[1] = (float)(v - (double)out[0]);
+  };
+  split(p.rho0, a->df_rho0);
+  split(2.0 * q->y * p.rho0, a->df_e0);
+  split(a->r2, a->df_r2);
+  split(0.5 * a->r2, a->df_half_r2);
+  split(q->y, a->df_inv_r2);
+  split(a->tshift, a->df_tshift);
+  split(a->tau_g_xi, a->df_taug_r);
+  split(p.g / q->r, a->df_g_r);
+  split(a->omega, a->df_omega);
+  split(a->omc, a->df_omc);
   return LBM_OK;
 }
 

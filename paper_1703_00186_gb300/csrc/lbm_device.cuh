@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -175,8 +176,14 @@ __device__ __forceinline__ void f2_add_mul(F2& acc, int k, float x) {
 __device__ __forceinline__ double f2_to_double(const F2& a) { return (double)a.hi + (double)a.lo; }
 
 // Moment sums of 37 float32 values (rho, Jx, Jy, Exi as in moment_sums),
-// accumulated in double-float and returned as float64.
-__device__ __forceinline__ Moments moment_sums_f2(const float (&d)[NPOP]) {
+// accumulated in double-float.
+struct MomentsDF {
+  DF rho, Jx, Jy, Exi;
+};
+
+__device__ __forceinline__ DF f2_norm(const F2& a) { return df_fast_two_sum(a.hi, a.lo); }
+
+__device__ __forceinline__ MomentsDF moment_sums_df(const float (&d)[NPOP]) {
   F2 r{d[0], 0.f}, jx{0.f, 0.f}, jy{0.f, 0.f}, e{0.f, 0.f};
   bool jx0 = true, jy0 = true, e0 = true;
 #pragma unroll
@@ -193,12 +200,7 @@ __device__ __forceinline__ Moments moment_sums_f2(const float (&d)[NPOP]) {
     if (e0) { e.hi = (float)sq(l) * d[l]; e.lo = fmaf((float)sq(l), d[l], -e.hi); e0 = false; }
     else f2_add_mul(e, sq(l), d[l]);
   }
-  Moments mo;
-  mo.rho = f2_to_double(r);
-  mo.Jx = f2_to_double(jx);
-  mo.Jy = f2_to_double(jy);
-  mo.Exi = f2_to_double(e);
-  return mo;
+  return {f2_norm(r), f2_norm(jx), f2_norm(jy), f2_norm(e)};
 }
 
 // Site state derived from the moments: velocity in xi units and temperature.
@@ -244,39 +246,56 @@ __device__ __forceinline__ void collide_fp64(double (&f)[NPOP], const LatticeArg
   }
 }
 
-// BGK collide on float32 deviations d_l = f_l - w_l rho0.  The moment sums
-// are accumulated in double-float (float64-class error, on the FP32 pipe)
-// and handed over as float64; the velocity, the temperature and the
-// temperature-dependent equilibrium coefficients are float64; the
-// per-population polynomial and relaxation are float32:
+__device__ __forceinline__ DF dfc(const float (&c)[2]) { return {c[0], c[1]}; }
+__device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.lo * p2}; }  // p2 a power of two
+
+// BGK collide on float32 deviations d_l = f_l - w_l rho0 (FP32 shifted storage):
 //   d_l <- (1 - omega) d_l + omega (f^eq_l - w_l rho0).
+// The moment sums, the velocity, the temperature and the temperature-dependent
+// equilibrium coefficients are carried in double-float (about 48 bits, on the
+// FP32 pipe; GB300 issues FP64 at 1/64 of the FP32 rate); the per-population
+// polynomial and the relaxation are float32.  Rounding the per-shell
+// coefficients to float32 leaves the discrete equilibrium's mass, momentum and
+// energy off by ~1e-8 relative in a way that repeats from step to step and so
+// accumulates; after the relaxation the conserved moments of the new
+// populations are therefore measured in double-float and the small defect is
+// put back on the rest and |xi| = 1 populations, so the collide conserves mass
+// and energy and adds exactly rho g to the momentum.
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
-  Moments mo = moment_sums_f2(d);
-  // add back the shift: sum w rho0 = rho0, sum w xi = 0, sum w |xi|^2 = D / r^2
-  mo.rho += a.rho0;
-  mo.Exi = fma(2.0 * a.inv_r2, a.rho0, mo.Exi);
-  const SiteFields sf = site_fields(mo, a);
-  const double theta = sf.T + a.tshift;
-  const double uys = sf.uy - a.tau_g_xi;
-  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
-  const EqCoef B = eq_coef(U2, theta);
-  const double rho = sf.rho;
-  // float64 -> float32 hand-over of the site coefficients
-  const float v_x = (float)(a.r2 * sf.ux), v_y = (float)(a.r2 * uys);
-  const float b10 = (float)B.B10, b11 = (float)B.B11, b20 = (float)B.B20, b21 = (float)B.B21;
-  const float rb00 = (float)fma(rho, B.B00, -a.rho0);  // rho B00 - rho0
-  const float rb01 = (float)(rho * B.B01), rb02 = (float)(rho * B.B02);
-  const float om = (float)a.omega, omc = (float)a.omc;
-  const float wr = (float)(a.omega * rho);
-  d[0] = fmaf(omc, d[0], om * (float)a.w_shell[0] * rb00);
+  const MomentsDF dev = moment_sums_df(d);
+  const DF rho = df_add(dev.rho, dfc(a.df_rho0));
+  const DF inv = df_rcp(rho);
+  const DF ux = df_mul(dev.Jx, inv), uy = df_mul(dev.Jy, inv);
+  const DF exi = df_add(dev.Exi, dfc(a.df_e0));
+  const DF usq = df_add(df_mul(ux, ux), df_mul(uy, uy));
+  const DF T = df_mul(df_sub(df_mul(exi, inv), usq), dfc(a.df_half_r2));
+  const DF theta = df_add(T, dfc(a.df_tshift));
+  const DF uys = df_sub(uy, dfc(a.df_taug_r));
+  const DF U2 = df_mul(df_add(df_mul(ux, ux), df_mul(uys, uys)), dfc(a.df_r2));
+  // equilibrium coefficients (see eq_coef), double-float
+  const DF th2 = df_mul(theta, theta);
+  const DF B20 = df_add(df_add(df_mul(U2, -0.25f), df_mul(theta, -1.5f)), 0.5f);
+  const DF B10 = df_add(df_add(df_scale2(U2, -0.5f), df_scale2(theta, -2.0f)), 1.0f);
+  const DF B00 = df_add(df_add(df_mul(U2, df_add(df_scale2(U2, 0.125f), -0.5f)),
+                               df_mul(theta, df_add(df_add(U2, -1.0f), theta))), 1.0f);
+  const DF B01 = df_mul(theta, df_sub(df_add(df_scale2(U2, -0.25f), 0.5f), theta));
+  const DF B02 = df_scale2(th2, 0.125f);
+  // hand-over to float32
+  const float v_x = df_mul(ux, dfc(a.df_r2)).hi, v_y = df_mul(uys, dfc(a.df_r2)).hi;
+  const float b10 = B10.hi, b11 = 0.5f * theta.hi, b20 = B20.hi, b21 = 0.25f * theta.hi;
+  const float rb00 = df_sub(df_mul(rho, B00), dfc(a.df_rho0)).hi;  // rho B00 - rho0
+  const float rb01 = df_mul(rho, B01).hi, rb02 = df_mul(rho, B02).hi;
+  const float om = a.omega_f, omc = a.omc_f;
+  const float wr = df_mul(rho, dfc(a.df_omega)).hi;
+  d[0] = fmaf(omc, d[0], om * a.w_shell_f[0] * rb00);
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
     const int j = pair_shell(k);
-    const float c2 = (float)a.c2_shell[j];
-    const float w = (float)a.w_shell[j];
+    const float c2 = a.c2_shell_f[j];
+    const float w = a.w_shell_f[j];
     const float A1 = fmaf(b11, c2, b10);
     const float A2 = fmaf(b21, c2, b20);
-    const float alpha = wr * w;                                   // omega w rho
+    const float alpha = wr * w;                                        // omega w rho
     const float beta = om * w * fmaf(c2, fmaf(c2, rb02, rb01), rb00);  // omega w (rho A0 - rho0)
     const float cu = pair_cu<float>(k, v_x, v_y);
     const float cu2 = cu * cu;
@@ -285,6 +304,23 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
     d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
     d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
   }
+  // conserved-moment correction (targets of the exact BGK update, xi units,
+  // deviation form): mass unchanged, Jy gains -rho g / r,
+  // Exi -> (1 - omega) Exi + omega (rho (|u'|^2 + D T') / r^2 - D rho0 / r^2)
+  const MomentsDF nw = moment_sums_df(d);
+  const DF tjy = df_sub(dev.Jy, df_mul(rho, dfc(a.df_g_r)));
+  const DF eeq = df_sub(df_mul(df_mul(rho, df_add(df_add(U2, df_scale2(theta, 2.0f)), 2.0f)), dfc(a.df_inv_r2)),
+                        dfc(a.df_e0));
+  const DF te = df_add(df_mul(dev.Exi, dfc(a.df_omc)), df_mul(eeq, dfc(a.df_omega)));
+  const float dm = df_sub(nw.rho, dev.rho).hi;
+  const float djx = df_sub(nw.Jx, dev.Jx).hi;
+  const float djy = df_sub(nw.Jy, tjy).hi;
+  const float de = df_sub(nw.Exi, te).hi;
+  d[0] += de - dm;
+  d[1] += (-0.5f * de - djx) * 0.5f;  // xi = (1, 0)
+  d[2] += (-0.5f * de + djx) * 0.5f;  // xi = (-1, 0)
+  d[3] += (-0.5f * de - djy) * 0.5f;  // xi = (0, 1)
+  d[4] += (-0.5f * de + djy) * 0.5f;  // xi = (0, -1)
 }
 
 // Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.

@@ -83,6 +83,20 @@ struct LatticeArgs {
   double q_top[NPOP];
   float w_rho0_f[NPOP];  // w_l rho0 as float (FP32 decode of bc inputs)
   double w_rho0[NPOP];   // w_l rho0
+  // float32 / double-float copies for the FP32-store collide
+  float w_shell_f[NSHELL];
+  float c2_shell_f[NSHELL];
+  float omega_f, omc_f;
+  float df_rho0[2];       // rho0
+  float df_e0[2];         // D rho0 / r^2: sum_l w_l |xi_l|^2 rho0
+  float df_r2[2];         // r^2
+  float df_half_r2[2];    // r^2 / 2
+  float df_inv_r2[2];     // 1 / r^2
+  float df_tshift[2];     // tau (1 - tau) g^2 / D - 1
+  float df_taug_r[2];     // tau g / r
+  float df_g_r[2];        // g / r
+  float df_omega[2];      // omega
+  float df_omc[2];        // 1 - omega
   unsigned int* status;  // device status word
 };
 

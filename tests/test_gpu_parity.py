@@ -173,3 +173,40 @@ def test_check_finite_and_status():
     lat.set_state(to_dev(f))
     assert not lat.check_finite()
     assert lat.status() == 0
+
+
+def _fields_err(a, b):
+    return [np.abs(x - y).max() / np.abs(y).max() for x, y in zip(a, b)]
+
+
+def test_fp32_shifted_error_stays_flat_over_1000_steps():
+    # 64 x 128 RT lattice, stable contrast T = 0.75 / 1.25, tau = 0.6: the
+    # float32 path against the float64 path (pinned to the oracle above).
+    # A conservation leak in the float32 collide grows the rho / T error
+    # linearly with the step count; storage rounding alone keeps it flat.
+    rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 0, delta=0.5)
+    kw = dict(tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
+    a = Lattice(64, 128, precision="fp64", **kw).init(rho, ux, uy, T)
+    b = Lattice(64, 128, precision="fp32", rho0=float(rho.mean()), **kw).init(rho, ux, uy, T)
+    errs = {}
+    for n in (200, 800):
+        a.step(n)
+        b.step(n)
+        ea = [t.cpu().numpy() for t in a.moments()]
+        eb = [t.cpu().numpy() for t in b.moments()]
+        errs[n] = _fields_err(eb, ea)
+    for n in (200, 800):
+        assert errs[n][0] <= 1e-6 and errs[n][3] <= 1e-6, errs
+    # no linear growth: 5x the steps, far less than 5x the error
+    assert errs[800][0] <= 2.5 * errs[200][0] + 1e-7 and errs[800][3] <= 2.5 * errs[200][3] + 1e-7, errs
+
+
+def test_fp32_shifted_conserves_mass():
+    lx, ly = 48, 40
+    rho, ux, uy, T = synth.random_fields(lx, ly, 77, umax=0.05, rho_range=(0.9, 1.1), t_range=(0.9, 1.1))
+    lat = Lattice(lx, ly, tau=0.7, g=0.0, precision="fp32", rho0=1.0, periodic_y=True)
+    lat.init(rho, ux, uy, T)
+    m0 = lat.moments()[0].sum().item()
+    lat.step(500)
+    m1 = lat.moments()[0].sum().item()
+    assert abs(m1 - m0) <= 1e-9 * m0, (m0, m1)
