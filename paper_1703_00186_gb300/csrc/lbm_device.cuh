@@ -203,6 +203,65 @@ __device__ __forceinline__ MomentsDF moment_sums_df(const float (&d)[NPOP]) {
   return {f2_norm(r), f2_norm(jx), f2_norm(jy), f2_norm(e)};
 }
 
+// Moment sums of 37 float32 values by an exact three-level split of every
+// value d = h + m + l (the "magic number" rounding of Dekker and Knuth:
+// adding and subtracting 1.5 * 2^k rounds to a multiple of 2^(k-23)):
+//   h: d rounded to a multiple of 2^-12; for |d| < 4 every weighted sum of
+//      the h (integer weights <= 10, 37 terms) stays below 2^23 grid steps,
+//      so it is exact in float32;
+//   m: the rest rounded to a multiple of 2^-34, read off as an integer
+//      (|m| 2^34 <= 2^21) and summed exactly in int32;
+//   l: the remainder, |l| <= 2^-35, summed in float32 (error < 2^-50).
+// The result is returned as double-float.  Values with |d| >= 4 (a diverged
+// lattice) are still summed, only no longer exactly.
+struct SplitAcc {
+  float h, l;
+  int m;
+};
+
+__device__ __forceinline__ DF split_result(const SplitAcc& a) {
+  // m * 2^-34 as two exact floats, then h + m + l in double-float
+  const float m_hi = (float)(a.m >> 12) * 0x1p-22f;
+  const float m_lo = (float)(a.m & 0xfff) * 0x1p-34f;
+  DF r = df_two_sum(a.h, m_hi);
+  r = df_add(r, m_lo);
+  return df_add(r, a.l);
+}
+
+__device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
+  constexpr float C1 = 3072.0f;        // 1.5 * 2^11: grid 2^-12
+  constexpr float C2 = 0x1.8p-11f;     // 1.5 * 2^-11: grid 2^-34
+  const int K2 = __float_as_int(C2);
+  SplitAcc r{0.f, 0.f, 0}, jx{0.f, 0.f, 0}, jy{0.f, 0.f, 0}, e{0.f, 0.f, 0};
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) {
+    const float h = (d[l] + C1) - C1;
+    const float rem = d[l] - h;
+    const float t = rem + C2;
+    const int m = __float_as_int(t) - K2;
+    const float lo = rem - (t - C2);
+    r.h += h;
+    r.m += m;
+    r.l += lo;
+    if (vx(l) != 0) {
+      jx.h = fmaf((float)vx(l), h, jx.h);
+      jx.m += vx(l) * m;
+      jx.l = fmaf((float)vx(l), lo, jx.l);
+    }
+    if (vy(l) != 0) {
+      jy.h = fmaf((float)vy(l), h, jy.h);
+      jy.m += vy(l) * m;
+      jy.l = fmaf((float)vy(l), lo, jy.l);
+    }
+    if (sq(l) != 0) {
+      e.h = fmaf((float)sq(l), h, e.h);
+      e.m += sq(l) * m;
+      e.l = fmaf((float)sq(l), lo, e.l);
+    }
+  }
+  return {split_result(r), split_result(jx), split_result(jy), split_result(e)};
+}
+
 // Site state derived from the moments: velocity in xi units and temperature.
 struct SiteFields {
   double rho, inv, ux, uy, T;  // u = r (ux, uy)
@@ -262,7 +321,7 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 // put back on the rest and |xi| = 1 populations, so the collide conserves mass
 // and energy and adds exactly rho g to the momentum.
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
-  const MomentsDF dev = moment_sums_df(d);
+  const MomentsDF dev = moment_sums_split(d);
   const DF rho = df_add(dev.rho, dfc(a.df_rho0));
   const DF inv = df_rcp(rho);
   const DF ux = df_mul(dev.Jx, inv), uy = df_mul(dev.Jy, inv);
@@ -304,14 +363,14 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
     d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
     d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
   }
-  // conserved-moment correction (targets of the exact BGK update, xi units,
-  // deviation form): mass unchanged, Jy gains -rho g / r,
-  // Exi -> (1 - omega) Exi + omega (rho (|u'|^2 + D T') / r^2 - D rho0 / r^2)
-  const MomentsDF nw = moment_sums_df(d);
-  const DF tjy = df_sub(dev.Jy, df_mul(rho, dfc(a.df_g_r)));
-  const DF eeq = df_sub(df_mul(df_mul(rho, df_add(df_add(U2, df_scale2(theta, 2.0f)), 2.0f)), dfc(a.df_inv_r2)),
-                        dfc(a.df_e0));
-  const DF te = df_add(df_mul(dev.Exi, dfc(a.df_omc)), df_mul(eeq, dfc(a.df_omega)));
+  // conserved-moment correction.  Targets of the exact BGK update with the
+  // equilibrium shift (omega tau = 1), deviation form, xi units, g_xi = g / r:
+  //   mass and Jx unchanged, Jy - rho g_xi, Exi - 2 g_xi Jy + rho g_xi^2.
+  const MomentsDF nw = moment_sums_split(d);
+  const DF gr = dfc(a.df_g_r);
+  const DF rg = df_mul(rho, gr);
+  const DF tjy = df_sub(dev.Jy, rg);
+  const DF te = df_add(df_sub(dev.Exi, df_scale2(df_mul(dev.Jy, gr), 2.0f)), df_mul(rg, gr));
   const float dm = df_sub(nw.rho, dev.rho).hi;
   const float djx = df_sub(nw.Jx, dev.Jx).hi;
   const float djy = df_sub(nw.Jy, tjy).hi;
