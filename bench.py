@@ -183,13 +183,17 @@ def cpu_baseline(lx, ly, budget_s):
 
 
 def _field_errors(a, b):
-    """max |a - b| / max |b| for each of rho, ux, uy, T (b is the float64 run)."""
+    """max |a - b| / max |b| for each of rho, ux, uy, T (b is the float64 run);
+    for the velocity also max |a - b| in units of the lattice sound speed
+    (sqrt(T0) = 1), since max |u| of a nearly still fluid is a poor scale."""
     names = ("rho", "ux", "uy", "T")
     out = {}
     for n, x, y in zip(names, a, b):
         d = (x - y).abs().max().item()
         scale = y.abs().max().item()
         out[n] = d / scale if scale > 0 else d
+        if n in ("ux", "uy"):
+            out[n + "_abs"] = d
     return out
 
 
