@@ -45,7 +45,19 @@ FP64_FLOP_PER_SITE = 547
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
-SECTIONS = ("fp64", "fp32", "adjoint", "e2e", "fp32_error", "rollout", "batch", "cpu")
+
+
+def _hbm_peak():
+    """HBM copy bandwidth measured on this GPU type (MEASURED_PEAKS.json)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json"
+    except (OSError, ValueError, KeyError):
+        return 6789.6, "fallback: earlier GB300 measurement"
+
+
+HBM_GBS_MEASURED, HBM_PEAK_SOURCE = _hbm_peak()
+SECTIONS = ("fp64", "fp32", "fp64df", "adjoint", "e2e", "fp32_error", "rollout", "batch", "cpu")
 
 
 def parse():
@@ -421,6 +433,15 @@ def main():
                        "finite": lat.check_finite()}
         del lat
         torch.cuda.empty_cache()
+    if "fp64df" in only:
+        lat, _ = rt_lattice(lx, ly, "fp64df")
+        lat.step(W)
+        barrier(torch, world)
+        t_ms = dist_max(time_steps(lat, K, torch), torch, world)
+        out["fp64df"] = {"ms": t_ms, "mlups": world * sites * K / (t_ms * 1e-3) / 1e6,
+                         "finite": lat.check_finite()}
+        del lat
+        torch.cuda.empty_cache()
     if "adjoint" in only:
         lat, _ = rt_lattice(lx, ly, "fp64")
         lat.step(W)
@@ -515,6 +536,15 @@ def main():
                              "speedup_vs_fp64": (f32["mlups"] / out["fp64"]["mlups"]) if "fp64" in out else None,
                              "hbm_gbs": BYTES_PER_SITE_FP32 * sites / t_launch / 1e9,
                              "finite_after_timed_steps": f32["finite"]}
+    if "fp64df" in out:
+        d = out["fp64df"]
+        t_launch = d["ms"] / K * 1e-3
+        res["fp64_df"] = {"mlups": d["mlups"], "ms_per_step": d["ms"] / K,
+                          "speedup_vs_fp64": (d["mlups"] / out["fp64"]["mlups"]) if "fp64" in out else None,
+                          "hbm_gbs": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9,
+                          "hbm_frac_of_measured": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9 / HBM_GBS_MEASURED,
+                          "arithmetic": "double-float (two float32 words, ~48 bits) on the FP32 pipe; float64 storage",
+                          "finite_after_timed_steps": d["finite"]}
     if "adjoint" in out:
         res["adjoint"] = out["adjoint"]
     if "e2e" in out:

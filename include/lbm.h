@@ -73,13 +73,22 @@ enum {
   LBM_ERR_STATE = -6      /* call not valid in the object's current state    */
 };
 
-enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+/* Storage and arithmetic of the step:
+ *   LBM_FP64         float64 populations, float64 arithmetic;
+ *   LBM_FP32_SHIFTED float32 deviations f_l - w_l rho0 (see collide notes);
+ *   LBM_FP64_DF      float64 populations; the collide runs in double-float
+ *                    arithmetic (two float32 words, about 48 significant
+ *                    bits) on the FP32 pipe, whose issue rate on GB300 is 64
+ *                    times the FP64 rate.  Propagate and bc are identical
+ *                    (bit-exact); every other call treats the state as
+ *                    LBM_FP64 (the adjoint linearises the float64 step). */
+enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_DF = 2 };
 enum { LBM_FLAG_PERIODIC_Y = 1 };  /* test mode: no walls, y periodic */
 
 typedef struct lbm_params {
   int32_t lx;         /* physical columns, >= 3 (periodic)                    */
   int32_t ly;         /* physical rows, >= 6 (walls at both ends)             */
-  int32_t precision;  /* LBM_FP64 or LBM_FP32_SHIFTED                         */
+  int32_t precision;  /* LBM_FP64, LBM_FP32_SHIFTED or LBM_FP64_DF             */
   int32_t flags;      /* LBM_FLAG_* bits                                      */
   double tau;         /* relaxation time, > 0.5 (eq. 1)                        */
   double g;           /* gravity magnitude, acting along -y                    */

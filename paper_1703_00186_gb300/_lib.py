@@ -21,6 +21,7 @@ LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
 LBM_FP64 = 0
 LBM_FP32_SHIFTED = 1
+LBM_FP64_DF = 2
 LBM_FLAG_PERIODIC_Y = 1
 LBM_NOALLOC_MAX_LX = 16384
 

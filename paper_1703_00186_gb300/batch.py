@@ -22,9 +22,9 @@ class Batch:
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.device = torch.device(device if device is not None else "cuda")
-        prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED}[precision]
+        prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED, "fp64df": L.LBM_FP64_DF}[precision]
         self.precision = precision
-        self.dtype = torch.float64 if prec == L.LBM_FP64 else torch.float32
+        self.dtype = torch.float32 if prec == L.LBM_FP32_SHIFTED else torch.float64
         self.specs = [dict(s) for s in specs]
         self.buffers = []
         descs = (L.LbmLatticeDesc * len(self.specs))()

@@ -88,4 +88,51 @@ __device__ __forceinline__ DF df_from_double(double v) {
 
 __device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (double)x.lo; }
 
+// float64 -> double-word without the FP64 pipe: integer arithmetic on the bit
+// pattern.  hi is x rounded to float32 (half-up on the 29 dropped mantissa
+// bits; the carry runs into the exponent field); the remainder x - hi is an
+// exact integer multiple of 2^(e - 1075), |multiple| <= 2^28, and lo is its
+// float32 rounding.  Representation error <= 2^-48 |x|.  |x| < 2^-126 gives 0;
+// |x| >= 2^128 (beyond float32) or non-finite x gives NaN, so a diverged state
+// stays visible.
+__device__ __forceinline__ DF df_from_double_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)(mag >> 52);
+  const unsigned long long H = (mag + (1ull << 28)) & ~((1ull << 29) - 1ull);
+  const int hbits = (int)(H >> 29) - (896 << 23);
+  const long long D = (long long)(mag - H);  // exact, |D| <= 2^28
+  const float scale = __int_as_float(max(e - 948, 1) << 23);
+  float lo = (float)(int)D * scale;
+  float hi = __int_as_float(hbits);
+  if (e < 897) { hi = 0.f; lo = 0.f; }
+  if (e > 1150) { hi = __int_as_float(0x7fc00000); lo = 0.f; }
+  if (e < 949) lo = 0.f;
+  return {__int_as_float(__float_as_int(hi) | (int)sign), __int_as_float(__float_as_int(lo) ^ (int)sign)};
+}
+
+// float32 -> float64 by bit arithmetic (exact for normal floats; zero and
+// subnormals give 0; NaN/Inf stay NaN/Inf).
+__device__ __forceinline__ double f32_to_f64_bits(float v) {
+  const unsigned int u = (unsigned int)__float_as_int(v);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  const unsigned long long ex = e == 255u ? 0x7FFull : (unsigned long long)(e + 896u);
+  const unsigned long long bits = e == 0u ? sign : (sign | (ex << 52) | m);
+  return __longlong_as_double((long long)bits);
+}
+
+// double-word -> float64: two exact conversions and one float64 add.
+__device__ __forceinline__ double df_to_double_bits(DF v) { return f32_to_f64_bits(v.hi) + f32_to_f64_bits(v.lo); }
+
+// x * k for a small integer k (exact scaling for powers of two).
+__device__ __forceinline__ DF df_mul_int(DF x, int k) {
+  if (k == 1) return x;
+  if (k == -1) return df_neg(x);
+  if (k == 2 || k == -2 || k == 4 || k == -4 || k == 8 || k == -8) return {x.hi * (float)k, x.lo * (float)k};
+  return df_mul(x, (float)k);
+}
+
 }  // namespace lbm

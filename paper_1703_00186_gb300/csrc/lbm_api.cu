@@ -56,7 +56,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     std::snprintf(err, errlen, "lattice too large");
     return LBM_ERR_INVALID;
   }
-  if (p.precision != LBM_FP64 && p.precision != LBM_FP32_SHIFTED) {
+  if (p.precision != LBM_FP64 && p.precision != LBM_FP32_SHIFTED && p.precision != LBM_FP64_DF) {
     std::snprintf(err, errlen, "unknown precision %d", p.precision);
     return LBM_ERR_INVALID;
   }
@@ -115,10 +115,19 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   split(p.g / q->r, a->df_g_r);
   split(a->omega, a->df_omega);
   split(a->omc, a->df_omc);
+  for (int j = 0; j < NSHELL; ++j) {
+    // w and c2 exactly as double-words from the double-double solution
+    a->df_w_shell[j][0] = (float)q->w_shell[j];
+    a->df_w_shell[j][1] = (float)((q->w_shell[j] - (double)a->df_w_shell[j][0]) + q->w_shell_lo[j]);
+    split(q->c2_shell[j], a->df_c2_shell[j]);
+  }
   return LBM_OK;
 }
 
 size_t element_size(int precision) { return precision == LBM_FP32_SHIFTED ? sizeof(float) : sizeof(double); }
+
+// Storage type of a precision mode (LBM_FP64_DF stores float64).
+int storage_prec(int precision) { return precision == LBM_FP32_SHIFTED ? LBM_FP32_SHIFTED : LBM_FP64; }
 
 }  // namespace lbm
 
@@ -160,7 +169,7 @@ extern "C" {
 
 size_t lbm_state_bytes(const lbm_params* p) {
   if (!p || p->lx < 3 || p->ly < 6) return 0;
-  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED) return 0;
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED && p->precision != LBM_FP64_DF) return 0;
   return (size_t)NPOP * (size_t)(p->ly + 2 * HALO) * (size_t)p->lx * element_size(p->precision);
 }
 
@@ -225,7 +234,7 @@ int lbm_set_stream(lbm_ctx* c, void* stream) {
 int lbm_init(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T) {
   if (!c) return LBM_ERR_INVALID;
   if (!rho || !ux || !uy || !T) return fail(c, LBM_ERR_INVALID, "lbm_init: NULL field");
-  return cuda_check(c, launch_init(c->p.precision, c->buf[c->cur], rho, ux, uy, T, c->args, c->stream),
+  return cuda_check(c, launch_init(storage_prec(c->p.precision), c->buf[c->cur], rho, ux, uy, T, c->args, c->stream),
                     "lbm_init");
 }
 
@@ -252,7 +261,7 @@ int lbm_moments(lbm_ctx* c, const void* f, double* rho, double* ux, double* uy, 
   if (!c) return LBM_ERR_INVALID;
   if (!rho && !ux && !uy && !T) return fail(c, LBM_ERR_INVALID, "lbm_moments: no output");
   if (!f) f = c->buf[c->cur];
-  return cuda_check(c, launch_moments(c->p.precision, f, rho, ux, uy, T, c->args, c->stream), "lbm_moments");
+  return cuda_check(c, launch_moments(storage_prec(c->p.precision), f, rho, ux, uy, T, c->args, c->stream), "lbm_moments");
 }
 
 int lbm_get_state(lbm_ctx* c, void* dst) {
@@ -272,14 +281,14 @@ int lbm_set_state(lbm_ctx* c, const void* src) {
 int lbm_propagate_bc(lbm_ctx* c, const void* src, void* dst) {
   if (!c) return LBM_ERR_INVALID;
   if (!src || !dst || src == dst) return fail(c, LBM_ERR_INVALID, "lbm_propagate_bc: bad buffers");
-  return cuda_check(c, launch_step(c->p.precision, false, src, dst, c->args, c->stream), "lbm_propagate_bc");
+  return cuda_check(c, launch_step(storage_prec(c->p.precision), false, src, dst, c->args, c->stream), "lbm_propagate_bc");
 }
 
 int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const double* lam_in, double* lam_out) {
   if (!c) return LBM_ERR_INVALID;
   if (!f_t || !lam_in || !lam_out || (const void*)lam_in == (const void*)lam_out)
     return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step: bad buffers");
-  return cuda_check(c, launch_adjoint(c->p.precision, f_t, lam_in, lam_out, c->args, c->stream),
+  return cuda_check(c, launch_adjoint(storage_prec(c->p.precision), f_t, lam_in, lam_out, c->args, c->stream),
                     "lbm_adjoint_step");
 }
 
@@ -287,7 +296,7 @@ int lbm_moments_vjp(lbm_ctx* c, const void* f, const double* g_rho, const double
                     const double* g_T, double* lam_out) {
   if (!c) return LBM_ERR_INVALID;
   if (!f || !lam_out) return fail(c, LBM_ERR_INVALID, "lbm_moments_vjp: bad buffers");
-  return cuda_check(c, launch_moments_vjp(c->p.precision, f, g_rho, g_ux, g_uy, g_T, lam_out, c->args, c->stream),
+  return cuda_check(c, launch_moments_vjp(storage_prec(c->p.precision), f, g_rho, g_ux, g_uy, g_T, lam_out, c->args, c->stream),
                     "lbm_moments_vjp");
 }
 
@@ -305,7 +314,7 @@ int lbm_check_finite(lbm_ctx* c, const void* f, int* ok) {
   if (!f) f = c->buf[c->cur];
   int rc = cuda_check(c, cudaMemsetAsync(c->dev + 1, 0, sizeof(unsigned int), c->stream), "lbm_check_finite");
   if (rc) return rc;
-  rc = cuda_check(c, launch_finite(c->p.precision, f, c->args, c->dev + 1, c->stream), "lbm_check_finite");
+  rc = cuda_check(c, launch_finite(storage_prec(c->p.precision), f, c->args, c->dev + 1, c->stream), "lbm_check_finite");
   if (rc) return rc;
   unsigned int flag = 0;
   rc = cuda_check(c, cudaMemcpyAsync(&flag, c->dev + 1, sizeof flag, cudaMemcpyDeviceToHost, c->stream),

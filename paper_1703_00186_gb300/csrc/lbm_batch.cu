@@ -23,6 +23,7 @@ namespace lbm {
 
 int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t errlen);
 size_t element_size(int precision);
+int storage_prec(int precision);
 cudaError_t launch_init(int prec, void* dst, const double* rho, const double* ux, const double* uy,
                         const double* T, const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_moments(int prec, const void* src, double* rho, double* ux, double* uy, double* T,
@@ -56,7 +57,7 @@ struct BCodec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-template <int PREC, int TBX, int TBY>
+template <int PREC, int TBX, int TBY, bool DFARITH = false>
 __global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry* __restrict__ ent,
                                                                const long long* __restrict__ tile_start,
                                                                int n, int parity) {
@@ -95,7 +96,9 @@ __global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry*
   T f[NPOP];
   pull(src, x, y, a, f);
   walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
-  if constexpr (PREC == LBM_FP64)
+  if constexpr (PREC == LBM_FP64 && DFARITH)
+    collide_fp64_df(f, a);
+  else if constexpr (PREC == LBM_FP64)
     collide_fp64(f, a);
   else
     collide_fp32(f, a);
@@ -107,7 +110,10 @@ template <int PREC, int I>
 cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long long* ts, int n, int parity,
                           cudaStream_t s) {
   constexpr int BX = kTileBX[I], BY = kTileBY[I];
-  batch_step_kernel<PREC, BX, BY><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, n, parity);
+  if constexpr (PREC == LBM_FP64_DF)
+    batch_step_kernel<LBM_FP64, BX, BY, true><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, n, parity);
+  else
+    batch_step_kernel<PREC, BX, BY><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, n, parity);
   return cudaGetLastError();
 }
 
@@ -165,6 +171,8 @@ int bcuda(lbm_batch* b, cudaError_t e, const char* what) {
 
 cudaError_t launch_batch(const lbm_batch* b, int parity, cudaStream_t s) {
   const int t = b->tile;
+  if (b->precision == LBM_FP64_DF)
+    return launch_tile<LBM_FP64_DF>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
   if (b->precision == LBM_FP64)
     return launch_tile<LBM_FP64>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
   return launch_tile<LBM_FP32_SHIFTED>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
@@ -230,7 +238,7 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
   if (!out) return LBM_ERR_INVALID;
   *out = nullptr;
   if (n < 1 || !descs) return LBM_ERR_INVALID;
-  if (precision != LBM_FP64 && precision != LBM_FP32_SHIFTED) return LBM_ERR_INVALID;
+  if (precision != LBM_FP64 && precision != LBM_FP32_SHIFTED && precision != LBM_FP64_DF) return LBM_ERR_INVALID;
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ERR_INVALID;
   b->n = n;
@@ -302,7 +310,7 @@ int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, con
   if (!b) return LBM_ERR_INVALID;
   if (i < 0 || i >= b->n || !rho || !ux || !uy || !T) return bfail(b, LBM_ERR_INVALID, "lbm_batch_init: bad args");
   void* cur = b->parity ? b->fb[i] : b->fa[i];
-  return bcuda(b, launch_init(b->precision, cur, rho, ux, uy, T, b->args[i], b->stream), "lbm_batch_init");
+  return bcuda(b, launch_init(storage_prec(b->precision), cur, rho, ux, uy, T, b->args[i], b->stream), "lbm_batch_init");
 }
 
 int lbm_batch_set_tile(lbm_batch* b, int tile) {
@@ -374,7 +382,7 @@ void* lbm_batch_current(const lbm_batch* b, int i) {
 int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy, double* T) {
   if (!b) return LBM_ERR_INVALID;
   if (i < 0 || i >= b->n) return bfail(b, LBM_ERR_INVALID, "lbm_batch_moments: bad index");
-  return bcuda(b, launch_moments(b->precision, lbm_batch_current(b, i), rho, ux, uy, T, b->args[i], b->stream),
+  return bcuda(b, launch_moments(storage_prec(b->precision), lbm_batch_current(b, i), rho, ux, uy, T, b->args[i], b->stream),
                "lbm_batch_moments");
 }
 

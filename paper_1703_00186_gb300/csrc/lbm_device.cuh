@@ -382,6 +382,85 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
   d[4] += (-0.5f * de + djy) * 0.5f;  // xi = (0, -1)
 }
 
+// BGK collide on float64 populations with the arithmetic in double-float on
+// the FP32 pipe (about 48 significant bits; GB300 issues FP64 at 1/64 of the
+// FP32 rate).  The populations are converted to double-words and back by
+// integer arithmetic on their bit patterns, so only the final recombination
+// of each output uses the FP64 pipe (one add).  Same formulation as
+// collide_fp64: (+,-) pairs, per-shell coefficients, one reciprocal.
+__device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const LatticeArgs& a) {
+  DF g[NPOP];
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) g[l] = df_from_double_bits(f[l]);
+  // moment sums by pairs
+  DF sh[NSHELL];
+  bool sh0[NSHELL];
+#pragma unroll
+  for (int j = 0; j < NSHELL; ++j) sh0[j] = true;
+  DF Jx{0.f, 0.f}, Jy{0.f, 0.f};
+  bool jx0 = true, jy0 = true;
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const DF s = df_add(g[2 * k + 1], g[2 * k + 2]);
+    const DF d = df_sub(g[2 * k + 1], g[2 * k + 2]);
+    const int j = pair_shell(k);
+    if (sh0[j]) { sh[j] = s; sh0[j] = false; } else sh[j] = df_add(sh[j], s);
+    if (rep_x(k) != 0) {
+      const DF t = df_mul_int(d, rep_x(k));
+      if (jx0) { Jx = t; jx0 = false; } else Jx = df_add(Jx, t);
+    }
+    if (rep_y(k) != 0) {
+      const DF t = df_mul_int(d, rep_y(k));
+      if (jy0) { Jy = t; jy0 = false; } else Jy = df_add(Jy, t);
+    }
+  }
+  const DF rho = df_add(df_add(df_add(g[0], sh[1]), df_add(sh[2], sh[3])),
+                        df_add(df_add(sh[4], sh[5]), df_add(sh[6], sh[7])));
+  DF exi = sh[1];
+#pragma unroll
+  for (int j = 2; j < NSHELL; ++j) exi = df_add(exi, df_mul_int(sh[j], shell_sq(j)));
+  // site fields
+  const DF inv = df_rcp(rho);
+  const DF ux = df_mul(Jx, inv), uy = df_mul(Jy, inv);
+  const DF usq = df_add(df_mul(ux, ux), df_mul(uy, uy));
+  const DF T = df_mul(df_sub(df_mul(exi, inv), usq), dfc(a.df_half_r2));
+  const DF theta = df_add(T, dfc(a.df_tshift));
+  const DF uys = df_sub(uy, dfc(a.df_taug_r));
+  const DF U2 = df_mul(df_add(df_mul(ux, ux), df_mul(uys, uys)), dfc(a.df_r2));
+  const DF v_x = df_mul(ux, dfc(a.df_r2)), v_y = df_mul(uys, dfc(a.df_r2));
+  const DF th2 = df_mul(theta, theta);
+  const DF B20 = df_add(df_add(df_mul(U2, -0.25f), df_mul(theta, -1.5f)), 0.5f);
+  const DF B21 = df_scale2(theta, 0.25f);
+  const DF B10 = df_add(df_add(df_scale2(U2, -0.5f), df_scale2(theta, -2.0f)), 1.0f);
+  const DF B11 = df_scale2(theta, 0.5f);
+  const DF B00 = df_add(df_add(df_mul(U2, df_add(df_scale2(U2, 0.125f), -0.5f)),
+                               df_mul(theta, df_add(df_add(U2, -1.0f), theta))), 1.0f);
+  const DF B01 = df_mul(theta, df_sub(df_add(df_scale2(U2, -0.25f), 0.5f), theta));
+  const DF B02 = df_scale2(th2, 0.125f);
+  const DF wr = df_mul(rho, dfc(a.df_omega));
+  const DF omc = dfc(a.df_omc);
+  f[0] = df_to_double_bits(df_add(df_mul(g[0], omc), df_mul(df_mul(wr, dfc(a.df_w_shell[0])), B00)));
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int j = pair_shell(k);
+    const DF c2 = dfc(a.df_c2_shell[j]);
+    const DF A0 = df_add(df_mul(df_add(df_mul(B02, c2), B01), c2), B00);
+    const DF A1 = df_add(df_mul(B11, c2), B10);
+    const DF A2 = df_add(df_mul(B21, c2), B20);
+    const DF sc = df_mul(wr, dfc(a.df_w_shell[j]));
+    DF cu;
+    if (rep_x(k) == 0) cu = df_mul_int(v_y, rep_y(k));
+    else if (rep_y(k) == 0) cu = df_mul_int(v_x, rep_x(k));
+    else cu = df_add(df_mul_int(v_x, rep_x(k)), df_mul_int(v_y, rep_y(k)));
+    const DF cu2 = df_mul(cu, cu);
+    const DF E = df_add(df_mul(df_add(df_mul(cu2, DF{0x1.555556p-5f, -0x1.555556p-30f}), A2), cu2), A0);  // 1/24
+    const DF O = df_mul(df_add(df_mul(cu2, DF{0x1.555556p-3f, -0x1.555556p-28f}), A1), cu);               // 1/6
+    const DF sE = df_mul(sc, E), sO = df_mul(sc, O);
+    f[2 * k + 1] = df_to_double_bits(df_add(df_mul(g[2 * k + 1], omc), df_add(sE, sO)));
+    f[2 * k + 2] = df_to_double_bits(df_add(df_mul(g[2 * k + 2], omc), df_sub(sE, sO)));
+  }
+}
+
 // Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.
 __device__ __forceinline__ void equilibrium(double rho, double ux, double uy, double T,
                                             const LatticeArgs& a, double (&f)[NPOP]) {

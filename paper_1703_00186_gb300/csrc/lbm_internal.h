@@ -97,6 +97,8 @@ struct LatticeArgs {
   float df_g_r[2];        // g / r
   float df_omega[2];      // omega
   float df_omc[2];        // 1 - omega
+  float df_w_shell[NSHELL][2];
+  float df_c2_shell[NSHELL][2];
   unsigned int* status;  // device status word
 };
 

@@ -171,7 +171,7 @@ extern "C" int lbm_adjoint_step_noalloc(const lbm_params* p, const void* f_t, co
   if (wall_partials_ptr(&partials) != cudaSuccess) return LBM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const dim3 grid((unsigned)((a.lx + 31) / 32), (unsigned)((a.ly + 3) / 4)), block(32, 4);
-  if (p->precision == LBM_FP64)
+  if (p->precision != LBM_FP32_SHIFTED)
     noalloc_adjoint_kernel<LBM_FP64><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, partials, a);
   else
     noalloc_adjoint_kernel<LBM_FP32_SHIFTED><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, partials, a);

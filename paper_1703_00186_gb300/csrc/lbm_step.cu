@@ -37,7 +37,7 @@ struct Codec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-template <int PREC, bool COLLIDE>
+template <int PREC, bool COLLIDE, bool DFARITH = false>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a) {
   using T = typename Codec<PREC>::T;
@@ -51,7 +51,9 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
   pull(src, x, y, a, f);
   walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
   if (COLLIDE) {
-    if constexpr (PREC == LBM_FP64)
+    if constexpr (PREC == LBM_FP64 && DFARITH)
+      collide_fp64_df(f, a);
+    else if constexpr (PREC == LBM_FP64)
       collide_fp64(f, a);
     else
       collide_fp32(f, a);
@@ -121,7 +123,12 @@ static dim3 site_grid(const LatticeArgs& a) {
 cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a,
                         cudaStream_t s) {
   const dim3 grid = site_grid(a), block(BX, BY);
-  if (prec == LBM_FP64) {
+  if (prec == LBM_FP64_DF) {
+    if (collide)
+      step_kernel<LBM_FP64, true, true><<<grid, block, 0, s>>>(src, dst, a);
+    else
+      step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a);
+  } else if (prec == LBM_FP64) {
     if (collide)
       step_kernel<LBM_FP64, true><<<grid, block, 0, s>>>(src, dst, a);
     else

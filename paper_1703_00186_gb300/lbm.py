@@ -55,8 +55,8 @@ class Lattice:
         self.device = torch.device(device if device is not None else "cuda")
         self.lx, self.ly = int(lx), int(ly)
         self.precision = precision
-        prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED}[precision]
-        self.dtype = torch.float64 if prec == L.LBM_FP64 else torch.float32
+        prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED, "fp64df": L.LBM_FP64_DF}[precision]
+        self.dtype = torch.float32 if prec == L.LBM_FP32_SHIFTED else torch.float64
         self.params = L.LbmParams(self.lx, self.ly, prec, L.LBM_FLAG_PERIODIC_Y if periodic_y else 0,
                                   float(tau), float(g), float(t_top), float(t_bottom), float(rho0))
         self.tau, self.g, self.t_top, self.t_bottom, self.rho0 = tau, g, t_top, t_bottom, rho0

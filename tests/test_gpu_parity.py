@@ -210,3 +210,32 @@ def test_fp32_shifted_conserves_mass():
     lat.step(500)
     m1 = lat.moments()[0].sum().item()
     assert abs(m1 - m0) <= 1e-9 * m0, (m0, m1)
+
+
+# ---------------------------------------------------------------------------
+# float64 storage with the collide in double-float arithmetic (LBM_FP64_DF):
+# held to the same bar as the float64 path.
+
+@pytest.mark.parametrize("lx,ly", [(64, 128), (67, 45), (3, 6)])
+@pytest.mark.parametrize("periodic_y", [False, True])
+def test_one_step_parity_fp64df(lx, ly, periodic_y):
+    p = M.Params(lx, ly, tau=0.7, g=2e-3, t_top=0.8, t_bottom=1.2, periodic_y=periodic_y)
+    f = noisy_state(lx, ly, 200 + lx, eps=0.05)
+    want = M.step(f, p)
+    lat = make(p, precision="fp64df")
+    lat.set_state(to_dev(f))
+    lat.step(1)
+    got = lat.state().cpu().numpy()
+    assert np.isnan(got[:, :3]).all() and np.isnan(got[:, -3:]).all()
+    assert plane_err(got, want) <= 1e-12
+
+
+def test_rayleigh_taylor_64x128_100_steps_fp64df():
+    rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 0)
+    p = M.Params(64, 128, tau=0.8, g=1e-4, t_top=tt, t_bottom=tb)
+    f0 = M.init_state(rho, ux, uy, T)
+    lat = make(p, precision="fp64df")
+    lat.set_state(to_dev(f0))
+    lat.step(100)
+    want = M.run(f0, p, 100)
+    assert plane_err(lat.state().cpu().numpy(), want) <= 1e-12
