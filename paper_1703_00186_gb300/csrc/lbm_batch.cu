@@ -96,9 +96,12 @@ __global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry*
   T f[NPOP];
   pull(src, x, y, a, f);
   walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
-  if constexpr (PREC == LBM_FP64 && DFARITH)
-    collide_fp64_df(f, a);
-  else if constexpr (PREC == LBM_FP64)
+  if constexpr (PREC == LBM_FP64 && DFARITH) {
+    __shared__ double s_f[NPOP][TBX * TBY];
+    collide_fp64_df<TBX * TBY>(f, a, s_f, tid, dst, x, y);
+    return;
+  }
+  if constexpr (PREC == LBM_FP64)
     collide_fp64(f, a);
   else
     collide_fp32(f, a);

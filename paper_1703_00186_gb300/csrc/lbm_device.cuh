@@ -299,9 +299,9 @@ __device__ __forceinline__ void collide_fp64(double (&f)[NPOP], const LatticeArg
     const double cu = pair_cu<double>(k, v_x, v_y);
     const double cu2 = cu * cu;
     const double E = fma(cu2, fma(cu2, 1.0 / 24.0, A2), A0);
-    const double O = cu * fma(cu2, 1.0 / 6.0, A1);
-    f[2 * k + 1] = fma(a.omc, f[2 * k + 1], sc * (E + O));
-    f[2 * k + 2] = fma(a.omc, f[2 * k + 2], sc * (E - O));
+    const double sO = sc * (cu * fma(cu2, 1.0 / 6.0, A1));
+    f[2 * k + 1] = fma(a.omc, f[2 * k + 1], fma(sc, E, sO));    // sc (E + O)
+    f[2 * k + 2] = fma(a.omc, f[2 * k + 2], fma(sc, E, -sO));   // sc (E - O)
   }
 }
 
@@ -382,48 +382,34 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
   d[4] += (-0.5f * de + djy) * 0.5f;  // xi = (0, -1)
 }
 
-// BGK collide on float64 populations with the arithmetic in double-float on
-// the FP32 pipe (about 48 significant bits; GB300 issues FP64 at 1/64 of the
-// FP32 rate).  The populations are converted to double-words and back by
-// integer arithmetic on their bit patterns, so only the final recombination
-// of each output uses the FP64 pipe (one add).  Same formulation as
-// collide_fp64: (+,-) pairs, per-shell coefficients, one reciprocal.
-__device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const LatticeArgs& a) {
-  DF g[NPOP];
+// Per-pair constants for rolled loops: representative R_k and shell index.
+static __constant__ signed char c_pair_rep[NPAIR][2] = {
+    {1, 0}, {0, 1}, {1, 1}, {-1, 1}, {2, 0}, {0, 2}, {2, 1}, {1, 2}, {-1, 2},
+    {-2, 1}, {2, 2}, {-2, 2}, {3, 0}, {0, 3}, {3, 1}, {1, 3}, {-1, 3}, {-3, 1}};
+// first pair of shell j (j = 1..7), and one past the last
+__host__ __device__ constexpr int shell_first_pair(int j) {
+  return j == 1 ? 0 : j == 2 ? 2 : j == 3 ? 4 : j == 4 ? 6 : j == 5 ? 10 : j == 6 ? 12 : j == 7 ? 14 : 18;
+}
+
+// BGK collide on float64 populations, balancing the FP64 and FP32 pipes
+// (GB300 issues FP64 at 1/64 of the FP32 rate).  The moment sums, 1/rho, u and
+// T are float64 exactly as in collide_fp64; the temperature-dependent
+// coefficients and the per-population equilibrium polynomial run in
+// double-float (about 48 significant bits) on the FP32 pipe; the relaxation is
+// one float64 FMA, f <- (1 - omega) f + f^eq, with f^eq recombined from its two
+// words by one float64 add.  The pair loop is rolled (the populations are read
+// back from shared memory) to keep the instruction footprint small.  The
+// results are written to dst directly.
+template <int NT>
+__device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const LatticeArgs& a, double (*s_f)[NT],
+                                                int tid, double* __restrict__ dst, int x, int y) {
+  const Moments mo = moment_sums([&](int l) { return f[l]; });
+  const SiteFields sf = site_fields(mo, a);
 #pragma unroll
-  for (int l = 0; l < NPOP; ++l) g[l] = df_from_double_bits(f[l]);
-  // moment sums by pairs
-  DF sh[NSHELL];
-  bool sh0[NSHELL];
-#pragma unroll
-  for (int j = 0; j < NSHELL; ++j) sh0[j] = true;
-  DF Jx{0.f, 0.f}, Jy{0.f, 0.f};
-  bool jx0 = true, jy0 = true;
-#pragma unroll
-  for (int k = 0; k < NPAIR; ++k) {
-    const DF s = df_add(g[2 * k + 1], g[2 * k + 2]);
-    const DF d = df_sub(g[2 * k + 1], g[2 * k + 2]);
-    const int j = pair_shell(k);
-    if (sh0[j]) { sh[j] = s; sh0[j] = false; } else sh[j] = df_add(sh[j], s);
-    if (rep_x(k) != 0) {
-      const DF t = df_mul_int(d, rep_x(k));
-      if (jx0) { Jx = t; jx0 = false; } else Jx = df_add(Jx, t);
-    }
-    if (rep_y(k) != 0) {
-      const DF t = df_mul_int(d, rep_y(k));
-      if (jy0) { Jy = t; jy0 = false; } else Jy = df_add(Jy, t);
-    }
-  }
-  const DF rho = df_add(df_add(df_add(g[0], sh[1]), df_add(sh[2], sh[3])),
-                        df_add(df_add(sh[4], sh[5]), df_add(sh[6], sh[7])));
-  DF exi = sh[1];
-#pragma unroll
-  for (int j = 2; j < NSHELL; ++j) exi = df_add(exi, df_mul_int(sh[j], shell_sq(j)));
-  // site fields
-  const DF inv = df_rcp(rho);
-  const DF ux = df_mul(Jx, inv), uy = df_mul(Jy, inv);
-  const DF usq = df_add(df_mul(ux, ux), df_mul(uy, uy));
-  const DF T = df_mul(df_sub(df_mul(exi, inv), usq), dfc(a.df_half_r2));
+  for (int l = 1; l < NPOP; ++l) s_f[l][tid] = f[l];
+  const DF rho = df_from_double_bits(sf.rho);
+  const DF ux = df_from_double_bits(sf.ux), uy = df_from_double_bits(sf.uy);
+  const DF T = df_from_double_bits(sf.T);
   const DF theta = df_add(T, dfc(a.df_tshift));
   const DF uys = df_sub(uy, dfc(a.df_taug_r));
   const DF U2 = df_mul(df_add(df_mul(ux, ux), df_mul(uys, uys)), dfc(a.df_r2));
@@ -438,26 +424,26 @@ __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const Lattice
   const DF B01 = df_mul(theta, df_sub(df_add(df_scale2(U2, -0.25f), 0.5f), theta));
   const DF B02 = df_scale2(th2, 0.125f);
   const DF wr = df_mul(rho, dfc(a.df_omega));
-  const DF omc = dfc(a.df_omc);
-  f[0] = df_to_double_bits(df_add(df_mul(g[0], omc), df_mul(df_mul(wr, dfc(a.df_w_shell[0])), B00)));
+  dst[sidx(a, 0, y, x)] = fma(a.omc, f[0], df_to_double_bits(df_mul(df_mul(wr, dfc(a.df_w_shell[0])), B00)));
 #pragma unroll
-  for (int k = 0; k < NPAIR; ++k) {
-    const int j = pair_shell(k);
+  for (int j = 1; j < NSHELL; ++j) {
     const DF c2 = dfc(a.df_c2_shell[j]);
     const DF A0 = df_add(df_mul(df_add(df_mul(B02, c2), B01), c2), B00);
     const DF A1 = df_add(df_mul(B11, c2), B10);
     const DF A2 = df_add(df_mul(B21, c2), B20);
     const DF sc = df_mul(wr, dfc(a.df_w_shell[j]));
-    DF cu;
-    if (rep_x(k) == 0) cu = df_mul_int(v_y, rep_y(k));
-    else if (rep_y(k) == 0) cu = df_mul_int(v_x, rep_x(k));
-    else cu = df_add(df_mul_int(v_x, rep_x(k)), df_mul_int(v_y, rep_y(k)));
-    const DF cu2 = df_mul(cu, cu);
-    const DF E = df_add(df_mul(df_add(df_mul(cu2, DF{0x1.555556p-5f, -0x1.555556p-30f}), A2), cu2), A0);  // 1/24
-    const DF O = df_mul(df_add(df_mul(cu2, DF{0x1.555556p-3f, -0x1.555556p-28f}), A1), cu);               // 1/6
-    const DF sE = df_mul(sc, E), sO = df_mul(sc, O);
-    f[2 * k + 1] = df_to_double_bits(df_add(df_mul(g[2 * k + 1], omc), df_add(sE, sO)));
-    f[2 * k + 2] = df_to_double_bits(df_add(df_mul(g[2 * k + 2], omc), df_sub(sE, sO)));
+#pragma unroll 1
+    for (int k = shell_first_pair(j); k < shell_first_pair(j + 1); ++k) {
+      const float rx = (float)c_pair_rep[k][0], ry = (float)c_pair_rep[k][1];
+      const DF cu = df_add(df_mul(v_x, rx), df_mul(v_y, ry));
+      const DF cu2 = df_mul(cu, cu);
+      const DF E = df_add(df_mul(df_add(df_mul(cu2, DF{0x1.555556p-5f, -0x1.555556p-30f}), A2), cu2), A0);  // 1/24
+      const DF O = df_mul(df_add(df_mul(cu2, DF{0x1.555556p-3f, -0x1.555556p-28f}), A1), cu);               // 1/6
+      const DF sE = df_mul(sc, E), sO = df_mul(sc, O);
+      const int lp = 2 * k + 1, lm = 2 * k + 2;
+      dst[sidx(a, lp, y, x)] = fma(a.omc, s_f[lp][tid], df_to_double_bits(df_add(sE, sO)));
+      dst[sidx(a, lm, y, x)] = fma(a.omc, s_f[lm][tid], df_to_double_bits(df_sub(sE, sO)));
+    }
   }
 }
 

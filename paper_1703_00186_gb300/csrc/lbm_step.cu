@@ -50,10 +50,15 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
   T f[NPOP];
   pull(src, x, y, a, f);
   walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+  if constexpr (PREC == LBM_FP64 && DFARITH) {
+    if (COLLIDE) {
+      __shared__ double s_f[NPOP][BX * BY];
+      collide_fp64_df<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
+      return;
+    }
+  }
   if (COLLIDE) {
-    if constexpr (PREC == LBM_FP64 && DFARITH)
-      collide_fp64_df(f, a);
-    else if constexpr (PREC == LBM_FP64)
+    if constexpr (PREC == LBM_FP64)
       collide_fp64(f, a);
     else
       collide_fp32(f, a);
