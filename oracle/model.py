@@ -301,6 +301,58 @@ def collide(ft, p: Params):
     return out
 
 
+# --------------------------------------------------------------------------
+# Regularised collide (the Hermite projection the paper mentions, Sect. 2)
+# --------------------------------------------------------------------------
+
+def _hermite_stack():
+    """H^(1..4)(c_l) for all l, as arrays (37, 2), (37, 2, 2), (37, 2, 2, 2), (37, 2, 2, 2, 2)."""
+    k = K()
+    hs = [_hermite_tensors(k["c"][l]) for l in range(NPOP)]
+    return [np.stack([h[i] for h in hs]) for i in range(4)]
+
+
+def hermite_project(fp):
+    """Projection onto the Hermite polynomials of order <= 4 (weight w):
+    (Pi f)_l = w_l sum_{n<=4} a^(n) : H^(n)(c_l) / n!,  a^(n) = sum_m f_m H^(n)(c_m).
+    fp has shape (37, ...)."""
+    H1, H2, H3, H4 = _hermite_stack()
+    a0 = fp.sum(axis=0)
+    a1 = np.einsum("p...,pi->...i", fp, H1)
+    a2 = np.einsum("p...,pij->...ij", fp, H2)
+    a3 = np.einsum("p...,pijk->...ijk", fp, H3)
+    a4 = np.einsum("p...,pijkm->...ijkm", fp, H4)
+    out = (a0[None]
+           + np.einsum("...i,pi->p...", a1, H1)
+           + np.einsum("...ij,pij->p...", a2, H2) / 2.0
+           + np.einsum("...ijk,pijk->p...", a3, H3) / 6.0
+           + np.einsum("...ijkm,pijkm->p...", a4, H4) / 24.0)
+    w = K()["w"].reshape((NPOP,) + (1,) * (fp.ndim - 1))
+    return w * out
+
+
+def collide_regularized(ft, p: Params):
+    """Regularised BGK: the non-equilibrium part is projected onto the order-<=4
+    Hermite space before relaxing,
+      f <- f^eq + (1 - 1/tau) Pi(f - f^eq),
+    with the same moments, gravity shift and equilibrium as collide().  Pi keeps
+    every moment of order <= 4, so mass, momentum (+ rho g) and energy change
+    exactly as in plain BGK; the components outside the Hermite space are
+    removed instead of relaxed."""
+    out = np.full_like(ft, np.nan)
+    fp = physical(ft)
+    rho, ux, uy, T = moments(fp)
+    uys = uy - p.tau * p.g
+    Ts = T + p.tau * (1.0 - p.tau) * p.g * p.g / D
+    feq = equilibrium(rho, ux, uys, Ts)
+    out[:, HALO:-HALO, :] = feq + (1.0 - 1.0 / p.tau) * hermite_project(fp - feq)
+    return out
+
+
+def step_regularized(f, p: Params):
+    return collide_regularized(propagate_bc(f, p), p)
+
+
 def propagate_bc(f, p: Params):
     return bc(propagate(f, p), f, p)
 
