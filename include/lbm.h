@@ -83,7 +83,16 @@ enum {
  *                    (bit-exact); every other call treats the state as
  *                    LBM_FP64 (the adjoint linearises the float64 step). */
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_DF = 2 };
-enum { LBM_FLAG_PERIODIC_Y = 1 };  /* test mode: no walls, y periodic */
+enum {
+  LBM_FLAG_PERIODIC_Y = 1,   /* test mode: no walls, y periodic */
+  /* Regularised collide (LBM_FP64 only): the populations are projected onto
+   * the velocity polynomials of degree <= 4 (the tensor Hermite polynomials of
+   * order <= 4, weight w) before relaxing, f <- f^eq + (1 - omega) Pi(f - f^eq):
+   * the "projection onto a basis of Hermite polynomials" of Sect. 2.  Mass,
+   * momentum and energy change exactly as in plain BGK.  The adjoint calls
+   * refuse contexts with this flag. */
+  LBM_FLAG_REGULARIZED = 2
+};
 
 typedef struct lbm_params {
   int32_t lx;         /* physical columns, >= 3 (periodic)                    */

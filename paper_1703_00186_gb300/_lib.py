@@ -23,6 +23,7 @@ LBM_FP64 = 0
 LBM_FP32_SHIFTED = 1
 LBM_FP64_DF = 2
 LBM_FLAG_PERIODIC_Y = 1
+LBM_FLAG_REGULARIZED = 2
 LBM_NOALLOC_MAX_LX = 16384
 
 c_int = ctypes.c_int

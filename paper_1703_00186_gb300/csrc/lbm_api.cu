@@ -65,8 +65,12 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     std::snprintf(err, errlen, "invalid physical parameters (need tau > 0.5, finite g, T_wall > 0)");
     return LBM_ERR_INVALID;
   }
-  if (p.flags & ~LBM_FLAG_PERIODIC_Y) {
+  if (p.flags & ~(LBM_FLAG_PERIODIC_Y | LBM_FLAG_REGULARIZED)) {
     std::snprintf(err, errlen, "unknown flags 0x%x", p.flags);
+    return LBM_ERR_INVALID;
+  }
+  if ((p.flags & LBM_FLAG_REGULARIZED) && p.precision != LBM_FP64) {
+    std::snprintf(err, errlen, "the regularised collide is implemented for LBM_FP64 only");
     return LBM_ERR_INVALID;
   }
   const Quadrature* q = quadrature(err, errlen);
@@ -76,6 +80,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->ly = p.ly;
   a->plane = (long long)(p.ly + 2 * HALO) * p.lx;
   a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;
+  a->regularized = (p.flags & LBM_FLAG_REGULARIZED) ? 1 : 0;
   a->tau = p.tau;
   a->omega = 1.0 / p.tau;
   a->omc = 1.0 - a->omega;
@@ -88,6 +93,10 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   for (int j = 0; j < NSHELL; ++j) {
     a->w_shell[j] = q->w_shell[j];
     a->c2_shell[j] = q->c2_shell[j];
+  }
+  if (a->regularized && regularization_gram_inverse(*q, a->ginv) != 0) {
+    std::snprintf(err, errlen, "singular Gram matrix");
+    return LBM_ERR_INVALID;
   }
   wall_ratios(*q, p.t_bottom, 0, a->q_bot);
   wall_ratios(*q, p.t_top, 1, a->q_top);
@@ -288,6 +297,8 @@ int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const double* lam_in, double* 
   if (!c) return LBM_ERR_INVALID;
   if (!f_t || !lam_in || !lam_out || (const void*)lam_in == (const void*)lam_out)
     return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step: bad buffers");
+  if (c->args.regularized)
+    return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step: no adjoint of the regularised collide");
   return cuda_check(c, launch_adjoint(storage_prec(c->p.precision), f_t, lam_in, lam_out, c->args, c->stream),
                     "lbm_adjoint_step");
 }

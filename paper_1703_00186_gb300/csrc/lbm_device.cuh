@@ -447,6 +447,122 @@ __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const Lattice
   }
 }
 
+__host__ __device__ constexpr int cpow(int v, int e) { return e == 0 ? 1 : v * cpow(v, e - 1); }
+
+// Regularised BGK collide in float64 (the Hermite projection of Sect. 2):
+//   f <- f^eq + (1 - omega) Pi(f - f^eq) = omega f^eq + (1 - omega) Pi f,
+// Pi the w-weighted projection onto the polynomials of degree <= 4 in the
+// velocity, which contain the equilibrium.  In integer-velocity monomials,
+// Pi f = w (sum_cd q_cd xi_x^c xi_y^d) with q = G^-1 N, N_cd = sum_l f_l
+// xi_x^c xi_y^d and G the (block-diagonal) Gram matrix of the monomials; the
+// new populations are w_l R(xi_l) with R = omega rho P + (1 - omega) q, P the
+// equilibrium polynomial expanded in the same monomials.
+__device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const LatticeArgs& a) {
+  double s[NPAIR], d[NPAIR];
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    s[k] = f[2 * k + 1] + f[2 * k + 2];
+    d[k] = f[2 * k + 1] - f[2 * k + 2];
+  }
+  // monomial moments: even total degree from s, odd from d; the rest
+  // population only enters N_00
+  auto Nm = [&](int c, int e) -> double {
+    const bool odd = ((c + e) & 1) != 0;
+    double acc = (c == 0 && e == 0) ? f[0] : -0.0;
+#pragma unroll
+    for (int k = 0; k < NPAIR; ++k) {
+      const int coef = cpow(rep_x(k), c) * cpow(rep_y(k), e);
+      if (coef != 0) acc = fma((double)coef, odd ? d[k] : s[k], acc);
+    }
+    return acc;
+  };
+  const double N00 = Nm(0, 0), N20 = Nm(2, 0), N02 = Nm(0, 2), N40 = Nm(4, 0), N22 = Nm(2, 2), N04 = Nm(0, 4);
+  const double N10 = Nm(1, 0), N30 = Nm(3, 0), N12 = Nm(1, 2);
+  const double N01 = Nm(0, 1), N03 = Nm(0, 3), N21 = Nm(2, 1);
+  const double N11 = Nm(1, 1), N31 = Nm(3, 1), N13 = Nm(1, 3);
+  // site fields (rho, J, E are monomial moments)
+  Moments mo;
+  mo.rho = N00;
+  mo.Jx = N10;
+  mo.Jy = N01;
+  mo.Exi = N20 + N02;
+  const SiteFields sf = site_fields(mo, a);
+  const double theta = sf.T + a.tshift;
+  const double uys = sf.uy - a.tau_g_xi;
+  const double vx_ = a.r2 * sf.ux, vy_ = a.r2 * uys;
+  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
+  const EqCoef B = eq_coef(U2, theta);
+  // equilibrium polynomial P in the monomials (cu = xi . v, c2 = r^2 |xi|^2)
+  const double r2 = a.r2, r4 = r2 * r2;
+  const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
+  const double P00 = B.B00;
+  const double P20 = fma(B.B01, r2, B.B20 * vx2);
+  const double P02 = fma(B.B01, r2, B.B20 * vy2);
+  const double P11 = 2.0 * B.B20 * vxy;
+  const double P40 = fma(B.B02, r4, fma(B.B21 * r2, vx2, vx2 * vx2 * (1.0 / 24.0)));
+  const double P04 = fma(B.B02, r4, fma(B.B21 * r2, vy2, vy2 * vy2 * (1.0 / 24.0)));
+  const double P22 = fma(2.0 * B.B02, r4, fma(B.B21 * r2, vx2 + vy2, vx2 * vy2 * 0.25));
+  const double P31 = vxy * fma(2.0 * B.B21, r2, vx2 * (1.0 / 6.0));
+  const double P13 = vxy * fma(2.0 * B.B21, r2, vy2 * (1.0 / 6.0));
+  const double P10 = B.B10 * vx_;
+  const double P01 = B.B10 * vy_;
+  const double P30 = vx_ * fma(B.B11, r2, vx2 * (1.0 / 6.0));
+  const double P03 = vy_ * fma(B.B11, r2, vy2 * (1.0 / 6.0));
+  const double P21 = vy_ * fma(B.B11, r2, vx2 * 0.5);
+  const double P12 = vx_ * fma(B.B11, r2, vy2 * 0.5);
+  // projection coefficients q = G^-1 N, block by block
+  const double* G = a.ginv;
+  const double NE[6] = {N00, N20, N02, N40, N22, N04};
+  double q[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc = fma(G[6 * i + j], NE[j], acc);
+    q[i] = acc;
+  }
+  auto blk3 = [&](int off, double n0, double n1, double n2, double (&o)[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i] = fma(G[off + 3 * i], n0, fma(G[off + 3 * i + 1], n1, G[off + 3 * i + 2] * n2));
+  };
+  double qoe[3], qeo[3], qoo[3];
+  blk3(36, N10, N30, N12, qoe);
+  blk3(45, N01, N03, N21, qeo);
+  blk3(54, N11, N31, N13, qoo);
+  // R = omega rho P + (1 - omega) q
+  const double wr = a.omega * sf.rho, om = a.omc;
+  const double R00 = fma(wr, P00, om * q[0]), R20 = fma(wr, P20, om * q[1]), R02 = fma(wr, P02, om * q[2]);
+  const double R40 = fma(wr, P40, om * q[3]), R22 = fma(wr, P22, om * q[4]), R04 = fma(wr, P04, om * q[5]);
+  const double R10 = fma(wr, P10, om * qoe[0]), R30 = fma(wr, P30, om * qoe[1]), R12 = fma(wr, P12, om * qoe[2]);
+  const double R01 = fma(wr, P01, om * qeo[0]), R03 = fma(wr, P03, om * qeo[1]), R21 = fma(wr, P21, om * qeo[2]);
+  const double R11 = fma(wr, P11, om * qoo[0]), R31 = fma(wr, P31, om * qoo[1]), R13 = fma(wr, P13, om * qoo[2]);
+  f[0] = a.w_shell[0] * R00;
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int x = rep_x(k), y = rep_y(k);
+    double ev = R00;
+    if (x) ev = fma((double)(x * x), R20, ev);
+    if (y) ev = fma((double)(y * y), R02, ev);
+    if (x) ev = fma((double)cpow(x, 4), R40, ev);
+    if (x && y) ev = fma((double)(x * x * y * y), R22, ev);
+    if (y) ev = fma((double)cpow(y, 4), R04, ev);
+    if (x && y) ev = fma((double)(x * y), R11, ev);
+    if (x && y) ev = fma((double)(cpow(x, 3) * y), R31, ev);
+    if (x && y) ev = fma((double)(x * cpow(y, 3)), R13, ev);
+    double od = -0.0;
+    if (x) od = fma((double)x, R10, od);
+    if (y) od = fma((double)y, R01, od);
+    if (x) od = fma((double)cpow(x, 3), R30, od);
+    if (x && y) od = fma((double)(x * y * y), R12, od);
+    if (y) od = fma((double)cpow(y, 3), R03, od);
+    if (x && y) od = fma((double)(x * x * y), R21, od);
+    const double w = a.w_shell[pair_shell(k)];
+    const double wod = w * od;
+    f[2 * k + 1] = fma(w, ev, wod);
+    f[2 * k + 2] = fma(w, ev, -wod);
+  }
+}
+
 // Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.
 __device__ __forceinline__ void equilibrium(double rho, double ux, double uy, double T,
                                             const LatticeArgs& a, double (&f)[NPOP]) {

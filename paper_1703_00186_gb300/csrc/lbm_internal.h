@@ -62,6 +62,9 @@ int solve_quadrature(Quadrature* out, char* err, size_t errlen);
 // phi_l = f^eq_l(1, 0, T_wall); wall = 0 bottom, 1 top.  Zero for l that is
 // not an unknown of that wall.
 void wall_ratios(const Quadrature& q, double t_wall, int wall, double out[NPOP]);
+// Inverse Gram blocks of the weighted velocity monomials for the regularised
+// collide (quadrature.cpp).  Returns 0 on success.
+int regularization_gram_inverse(const Quadrature& q, double out[63]);
 
 // Per-launch constants of a lattice, passed by value (kernel parameter space).
 struct LatticeArgs {
@@ -98,6 +101,8 @@ struct LatticeArgs {
   float df_omega[2];      // omega
   float df_omc[2];        // 1 - omega
   float df_w_shell[NSHELL][2];
+  int regularized;        // LBM_FLAG_REGULARIZED
+  double ginv[63];        // inverse Gram blocks EE(36) OE(9) EO(9) OO(9)
   float df_c2_shell[NSHELL][2];
   unsigned int* status;  // device status word
 };

@@ -164,6 +164,7 @@ extern "C" int lbm_adjoint_step_noalloc(const lbm_params* p, const void* f_t, co
   char err[256];
   const int rc = make_lattice_args(*p, &a, err, sizeof err);
   if (rc != LBM_OK) return rc;
+  if (a.regularized) return LBM_ERR_INVALID;
   if (reinterpret_cast<uintptr_t>(f_t) % element_size(p->precision) ||
       reinterpret_cast<uintptr_t>(lam_in) % sizeof(double) || reinterpret_cast<uintptr_t>(lam_out) % sizeof(double))
     return LBM_ERR_INVALID;

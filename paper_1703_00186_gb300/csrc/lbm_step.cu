@@ -37,7 +37,7 @@ struct Codec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-template <int PREC, bool COLLIDE, bool DFARITH = false>
+template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a) {
   using T = typename Codec<PREC>::T;
@@ -58,10 +58,13 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
     }
   }
   if (COLLIDE) {
-    if constexpr (PREC == LBM_FP64)
+    if constexpr (PREC == LBM_FP64 && REG) {
+      collide_fp64_reg(f, a);
+    } else if constexpr (PREC == LBM_FP64) {
       collide_fp64(f, a);
-    else
+    } else {
       collide_fp32(f, a);
+    }
   }
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
@@ -134,7 +137,9 @@ cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, cons
     else
       step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a);
   } else if (prec == LBM_FP64) {
-    if (collide)
+    if (collide && a.regularized)
+      step_kernel<LBM_FP64, true, false, true><<<grid, block, 0, s>>>(src, dst, a);
+    else if (collide)
       step_kernel<LBM_FP64, true><<<grid, block, 0, s>>>(src, dst, a);
     else
       step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a);

@@ -230,4 +230,64 @@ void wall_ratios(const Quadrature& q, double t_wall, int wall, double out[NPOP])
   }
 }
 
+// Inverse Gram blocks of the w-weighted monomials xi_x^c xi_y^d (c + d <= 4)
+// over the 37 velocities, split by the parity of (c, d):
+//   EE [1, x^2, y^2, x^4, x^2 y^2, y^4], OE [x, x^3, x y^2],
+//   EO [y, y^3, x^2 y], OO [x y, x^3 y, x y^3],
+// inverted in double-double and rounded once.  Output order: EE (36), OE (9),
+// EO (9), OO (9), each row-major.
+namespace {
+bool invert_dd(int n, dd (*A)[6], dd (*X)[6]) {
+  dd M[6][12];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = j < n ? A[i][j] : D(j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (dabs(M[r][c]) > dabs(M[p][c])) p = r;
+    if (M[p][c].hi == 0.0) return false;
+    if (p != c)
+      for (int k = 0; k < 2 * n; ++k) std::swap(M[c][k], M[p][k]);
+    const dd inv = D(1.0) / M[c][c];
+    for (int k = 0; k < 2 * n; ++k) M[c][k] = M[c][k] * inv;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const dd f = M[r][c];
+        for (int k = 0; k < 2 * n; ++k) M[r][k] = M[r][k] - f * M[c][k];
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) X[i][j] = M[i][n + j];
+  return true;
+}
+}  // namespace
+
+int regularization_gram_inverse(const Quadrature& q, double out[63]) {
+  static const int blocks[4][6][2] = {
+      {{0, 0}, {2, 0}, {0, 2}, {4, 0}, {2, 2}, {0, 4}},
+      {{1, 0}, {3, 0}, {1, 2}, {0, 0}, {0, 0}, {0, 0}},
+      {{0, 1}, {0, 3}, {2, 1}, {0, 0}, {0, 0}, {0, 0}},
+      {{1, 1}, {3, 1}, {1, 3}, {0, 0}, {0, 0}, {0, 0}}};
+  static const int sizes[4] = {6, 3, 3, 3};
+  int o = 0;
+  for (int b = 0; b < 4; ++b) {
+    const int n = sizes[b];
+    dd G[6][6], X[6][6];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        dd acc = D(0.0);
+        for (int l = 0; l < NPOP; ++l) {
+          const double m = ipow(vx(l), blocks[b][i][0] + blocks[b][j][0]) * ipow(vy(l), blocks[b][i][1] + blocks[b][j][1]);
+          const int s = shell_index(sq(l));
+          acc = acc + dd{q.w_shell[s], q.w_shell_lo[s]} * D(m);
+        }
+        G[i][j] = acc;
+      }
+    if (!invert_dd(n, G, X)) return -1;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) out[o++] = X[i][j].hi;
+  }
+  return 0;
+}
+
 }  // namespace lbm

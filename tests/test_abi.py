@@ -61,3 +61,14 @@ def test_state_bytes_and_argument_checks_need_no_gpu(lib):
                           12345, None) == L.LBM_ERR_SIZE
     assert not ctx.value
     assert lib.lbm_step(None, 1) == L.LBM_ERR_INVALID
+
+
+def test_regularized_flag_only_with_fp64(lib):
+    from paper_1703_00186_gb300 import _lib as L
+    ctx = ctypes.c_void_p()
+    p = L.LbmParams(64, 128, L.LBM_FP32_SHIFTED, L.LBM_FLAG_REGULARIZED, 0.8, 0.0, 1.0, 1.0, 1.0)
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(p), ctypes.c_void_p(8), ctypes.c_void_p(16),
+                          lib.lbm_state_bytes(ctypes.byref(p)), None) == L.LBM_ERR_INVALID
+    bad = L.LbmParams(64, 128, L.LBM_FP64, 8, 0.8, 0.0, 1.0, 1.0, 1.0)   # unknown flag bit
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(bad), ctypes.c_void_p(8), ctypes.c_void_p(16),
+                          lib.lbm_state_bytes(ctypes.byref(bad)), None) == L.LBM_ERR_INVALID

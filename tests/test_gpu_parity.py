@@ -239,3 +239,41 @@ def test_rayleigh_taylor_64x128_100_steps_fp64df():
     lat.step(100)
     want = M.run(f0, p, 100)
     assert plane_err(lat.state().cpu().numpy(), want) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Regularised collide (LBM_FLAG_REGULARIZED): the oracle projects with explicit
+# tensor Hermite polynomials; the kernel with velocity monomials and an inverse
+# Gram matrix.  Same float64 bar.
+
+@pytest.mark.parametrize("lx,ly", [(40, 24), (67, 45), (3, 6)])
+@pytest.mark.parametrize("periodic_y", [False, True])
+def test_one_step_parity_regularized(lx, ly, periodic_y):
+    p = M.Params(lx, ly, tau=0.7, g=2e-3, t_top=0.8, t_bottom=1.2, periodic_y=periodic_y)
+    f = noisy_state(lx, ly, 400 + lx, eps=0.05)
+    want = M.step_regularized(f, p)
+    lat = Lattice(lx, ly, tau=p.tau, g=p.g, t_top=p.t_top, t_bottom=p.t_bottom, periodic_y=periodic_y,
+                  regularized=True)
+    lat.set_state(to_dev(f))
+    lat.step(1)
+    assert plane_err(lat.state().cpu().numpy(), want) <= 1e-12
+
+
+def test_rayleigh_taylor_64x128_100_steps_regularized():
+    rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 0)
+    p = M.Params(64, 128, tau=0.8, g=1e-4, t_top=tt, t_bottom=tb)
+    f = M.init_state(rho, ux, uy, T)
+    lat = Lattice(64, 128, tau=p.tau, g=p.g, t_top=tt, t_bottom=tb, regularized=True)
+    lat.set_state(to_dev(f))
+    lat.step(100)
+    for _ in range(100):
+        f = M.step_regularized(f, p)
+    assert plane_err(lat.state().cpu().numpy(), f) <= 1e-12
+
+
+def test_adjoint_refuses_regularized_context():
+    from paper_1703_00186_gb300._lib import LBMError
+    lat = Lattice(16, 12, tau=0.8, regularized=True)
+    f = lat.new_state(0.1)
+    with pytest.raises(LBMError):
+        lat.adjoint_step(f, lat.new_cotangent(0.0))
