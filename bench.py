@@ -57,7 +57,7 @@ def _hbm_peak():
 
 
 HBM_GBS_MEASURED, HBM_PEAK_SOURCE = _hbm_peak()
-SECTIONS = ("fp64", "fp32", "fp64df", "regularized", "adjoint", "e2e", "fp32_error", "rollout", "batch", "cpu")
+SECTIONS = ("fp64", "fp32", "fp64df", "regularized", "observe", "adjoint", "e2e", "fp32_error", "rollout", "batch", "cpu")
 
 
 def parse():
@@ -454,6 +454,25 @@ def main():
                               "finite": lat.check_finite()}
         del lat
         torch.cuda.empty_cache()
+    if "observe" in only:
+        lat, _ = rt_lattice(lx, ly, "fp64")
+        lat.step(W)
+        barrier(torch, world)
+        s = lat.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ko = max(2, K // 5)
+        lat.step_observe(2, 1)
+        torch.cuda.synchronize()
+        e0.record(s)
+        lat.step_observe(ko, 1)
+        e1.record(s)
+        e1.synchronize()
+        t_obs = dist_max(e0.elapsed_time(e1) / ko, torch, world)
+        t_plain = dist_max(time_steps(lat, ko, torch) / ko, torch, world)
+        out["observe"] = {"observing_step_ms": t_obs, "plain_step_ms": t_plain, "overhead": t_obs / t_plain - 1.0}
+        del lat
+        torch.cuda.empty_cache()
     if "adjoint" in only:
         lat, _ = rt_lattice(lx, ly, "fp64")
         lat.step(W)
@@ -563,6 +582,9 @@ def main():
                               "vs_fp64_bgk": (d["mlups"] / out["fp64"]["mlups"]) if "fp64" in out else None,
                               "collide": "float64, Hermite projection of order <= 4 before relaxing",
                               "finite_after_timed_steps": d["finite"]}
+    if "observe" in out:
+        res["observables"] = {**out["observe"], "quantities": 8,
+                              "what": "row averages fused into the float64 step (every observing step)"}
     if "adjoint" in out:
         res["adjoint"] = out["adjoint"]
     if "e2e" in out:

@@ -154,6 +154,27 @@ void* lbm_current(const lbm_ctx* ctx);
 int lbm_moments(lbm_ctx* ctx, const void* f, double* rho, double* ux,
                 double* uy, double* T);
 
+/* Measurement routines (Sect. 2: averages of physical observables taken every
+ * several hundred or thousand steps).  LBM_NOBS quantities are averaged over x
+ * for every physical row y:
+ *   0 rho, 1 u_x, 2 u_y, 3 T, 4 T^2, 5 u_y T, 6 rho |u|^2 / 2, 7 rho u_y,
+ * with eq. (2) fields and the hydrodynamic (mid-step) velocity
+ * u = (sum c f - rho g_vec / 2) / rho, g_vec = (0, -g), of the stored state.
+ * Output: device double array [LBM_NOBS][ly].
+ * lbm_profiles: of state f (NULL = current); deterministic reduction. */
+#define LBM_NOBS 8
+int lbm_profiles(lbm_ctx* ctx, const void* f, double* out);
+
+/* Advance n >= 0 steps like lbm_step, and after every `every`-th step
+ * (steps every, 2 every, ...) store the row averages of the new state in the
+ * next record of `out` (device double array [n / every][LBM_NOBS][ly]).  The
+ * observing steps compute the averages in the step kernel itself from the
+ * moments the collide already forms (summation order across warps is not
+ * fixed: results agree with lbm_profiles to rounding).  LBM_FP64 contexts
+ * without LBM_FLAG_REGULARIZED only; every >= 1.  *records (host, may be NULL)
+ * receives the number of records written. */
+int lbm_step_observe(lbm_ctx* ctx, int n, int every, double* out, int* records);
+
 /* Checkpoint / restore: copy the current state to / from a caller buffer of
  * lbm_state_bytes() (device memory, or host memory the CUDA runtime can
  * address, e.g. pinned). */

@@ -25,6 +25,7 @@ LBM_FP64_DF = 2
 LBM_FLAG_PERIODIC_Y = 1
 LBM_FLAG_REGULARIZED = 2
 LBM_NOALLOC_MAX_LX = 16384
+LBM_NOBS = 8
 
 c_int = ctypes.c_int
 c_double = ctypes.c_double
@@ -58,6 +59,8 @@ SIGNATURES = {
     "lbm_step_from": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_current": (c_void_p, [c_void_p]),
     "lbm_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_profiles": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "lbm_step_observe": (c_int, [c_void_p, c_int, c_int, c_void_p, P(c_int)]),
     "lbm_get_state": (c_int, [c_void_p, c_void_p]),
     "lbm_set_state": (c_int, [c_void_p, c_void_p]),
     "lbm_propagate_bc": (c_int, [c_void_p, c_void_p, c_void_p]),

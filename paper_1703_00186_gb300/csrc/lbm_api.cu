@@ -20,6 +20,8 @@ cudaError_t launch_moments(int prec, const void* src, double* rho, double* ux, d
                            const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_finite(int prec, const void* src, const LatticeArgs& a, unsigned int* flag,
                           cudaStream_t s);
+cudaError_t launch_profiles(int prec, const void* src, double* out, const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_step_observe(const void* src, void* dst, const LatticeArgs& a, double* obs, cudaStream_t s);
 cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, double* lam_out,
                            const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux,
@@ -82,6 +84,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;
   a->regularized = (p.flags & LBM_FLAG_REGULARIZED) ? 1 : 0;
   a->tau = p.tau;
+  a->g = p.g;
   a->omega = 1.0 / p.tau;
   a->omc = 1.0 - a->omega;
   a->r = q->r;
@@ -271,6 +274,35 @@ int lbm_moments(lbm_ctx* c, const void* f, double* rho, double* ux, double* uy, 
   if (!rho && !ux && !uy && !T) return fail(c, LBM_ERR_INVALID, "lbm_moments: no output");
   if (!f) f = c->buf[c->cur];
   return cuda_check(c, launch_moments(storage_prec(c->p.precision), f, rho, ux, uy, T, c->args, c->stream), "lbm_moments");
+}
+
+int lbm_profiles(lbm_ctx* c, const void* f, double* out) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!out) return fail(c, LBM_ERR_INVALID, "lbm_profiles: NULL output");
+  if (!f) f = c->buf[c->cur];
+  return cuda_check(c, launch_profiles(storage_prec(c->p.precision), f, out, c->args, c->stream), "lbm_profiles");
+}
+
+int lbm_step_observe(lbm_ctx* c, int n, int every, double* out, int* records) {
+  if (!c) return LBM_ERR_INVALID;
+  if (n < 0 || every < 1 || (n >= every && !out)) return fail(c, LBM_ERR_INVALID, "lbm_step_observe: bad arguments");
+  if (c->p.precision != LBM_FP64 || c->args.regularized)
+    return fail(c, LBM_ERR_INVALID, "lbm_step_observe: plain LBM_FP64 contexts only");
+  int rec = 0;
+  for (int i = 1; i <= n; ++i) {
+    cudaError_t e;
+    if (i % every == 0) {
+      e = launch_step_observe(c->buf[c->cur], c->buf[1 - c->cur], c->args,
+                              out + (size_t)rec * LBM_NOBS * (size_t)c->p.ly, c->stream);
+      ++rec;
+    } else {
+      e = launch_step(c->p.precision, true, c->buf[c->cur], c->buf[1 - c->cur], c->args, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "lbm_step_observe");
+    c->cur ^= 1;
+  }
+  if (records) *records = rec;
+  return LBM_OK;
 }
 
 int lbm_get_state(lbm_ctx* c, void* dst) {

@@ -277,8 +277,9 @@ __device__ __forceinline__ SiteFields site_fields(const Moments& m, const Lattic
   return s;
 }
 
-// BGK collide in float64 (eq. 1) with the gravity equilibrium shift.
-__device__ __forceinline__ void collide_fp64(double (&f)[NPOP], const LatticeArgs& a) {
+// BGK collide in float64 (eq. 1) with the gravity equilibrium shift.  Returns
+// the pre-collide site fields (rho, u in xi units, T).
+__device__ __forceinline__ SiteFields collide_fp64(double (&f)[NPOP], const LatticeArgs& a) {
   const Moments mo = moment_sums([&](int l) { return f[l]; });
   const SiteFields sf = site_fields(mo, a);
   const double theta = sf.T + a.tshift;
@@ -303,6 +304,22 @@ __device__ __forceinline__ void collide_fp64(double (&f)[NPOP], const LatticeArg
     f[2 * k + 1] = fma(a.omc, f[2 * k + 1], fma(sc, E, sO));    // sc (E + O)
     f[2 * k + 2] = fma(a.omc, f[2 * k + 2], fma(sc, E, -sO));   // sc (E - O)
   }
+  return sf;
+}
+
+// Row-averaged observables of one site: rho, u_x, u_y, T, T^2, u_y T,
+// rho |u|^2 / 2, rho u_y, with the mid-step hydrodynamic velocity (physical
+// units) u_h = (u_x, u_y + g / 2) of the stored post-collide state.
+constexpr int NOBS = 8;
+__device__ __forceinline__ void site_observables(double rho, double ux, double uy_h, double T, double (&o)[NOBS]) {
+  o[0] = rho;
+  o[1] = ux;
+  o[2] = uy_h;
+  o[3] = T;
+  o[4] = T * T;
+  o[5] = uy_h * T;
+  o[6] = 0.5 * rho * fma(ux, ux, uy_h * uy_h);
+  o[7] = rho * uy_h;
 }
 
 __device__ __forceinline__ DF dfc(const float (&c)[2]) { return {c[0], c[1]}; }

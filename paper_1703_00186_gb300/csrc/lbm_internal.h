@@ -79,6 +79,7 @@ struct LatticeArgs {
   double tau_g_xi;       // tau g / r: the gravity shift of u in xi units
   double tshift;         // tau (1 - tau) g^2 / D - 1: theta = T + tshift
   double tau;
+  double g;              // gravity magnitude (along -y)
   double rho0;           // FP32 shift density
   double w_shell[NSHELL];
   double c2_shell[NSHELL];

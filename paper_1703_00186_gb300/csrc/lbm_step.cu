@@ -37,9 +37,10 @@ struct Codec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false>
+template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, bool OBS = false>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ src_,
-                                                       void* __restrict__ dst_, LatticeArgs a) {
+                                                       void* __restrict__ dst_, LatticeArgs a,
+                                                       double* __restrict__ obs = nullptr) {
   using T = typename Codec<PREC>::T;
   const int x = blockIdx.x * BX + threadIdx.x;
   const int y = blockIdx.y * BY + threadIdx.y;
@@ -60,6 +61,24 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
   if (COLLIDE) {
     if constexpr (PREC == LBM_FP64 && REG) {
       collide_fp64_reg(f, a);
+    } else if constexpr (PREC == LBM_FP64 && OBS) {
+      // measurement epilogue: the collide leaves rho and T unchanged and adds
+      // the impulse g_vec to u, so the new state's mid-step velocity is the
+      // pre-collide u + g_vec / 2; warp sums (one row segment) go to the row
+      // totals with one atomic add per quantity.
+      const SiteFields sf = collide_fp64(f, a);
+      double o[NOBS];
+      site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy - 0.5 * a.g, sf.T, o);
+      const unsigned mask = __activemask();
+#pragma unroll
+      for (int i = 0; i < NOBS; ++i) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) o[i] += __shfl_down_sync(mask, o[i], off);
+      }
+      if ((threadIdx.x & 31) == __ffs(mask) - 1) {
+#pragma unroll
+        for (int i = 0; i < NOBS; ++i) atomicAdd(obs + (long long)i * a.ly + y, o[i]);
+      }
     } else if constexpr (PREC == LBM_FP64) {
       collide_fp64(f, a);
     } else {
@@ -124,6 +143,46 @@ __global__ void finite_kernel(const void* __restrict__ src_, LatticeArgs a, unsi
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
+// Row averages of the observables of a stored state (deterministic: fixed
+// per-thread strides and a fixed-order tree reduction).  One block per row.
+template <int PREC>
+__global__ void __launch_bounds__(256) profiles_kernel(const void* __restrict__ src_, double* __restrict__ out,
+                                                       LatticeArgs a) {
+  using S = typename Codec<PREC>::T;
+  const int y = blockIdx.x;
+  const S* src = static_cast<const S*>(src_);
+  Codec<PREC> codec{&a};
+  double acc[NOBS];
+#pragma unroll
+  for (int i = 0; i < NOBS; ++i) acc[i] = 0.0;
+  for (int x = threadIdx.x; x < a.lx; x += blockDim.x) {
+    const Moments mo = moment_sums([&](int l) { return codec(l, src[sidx(a, l, y, x)]); });
+    const SiteFields sf = site_fields(mo, a);
+    double o[NOBS];
+    site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy + 0.5 * a.g, sf.T, o);
+#pragma unroll
+    for (int i = 0; i < NOBS; ++i) acc[i] += o[i];
+  }
+  __shared__ double red[NOBS][256];
+#pragma unroll
+  for (int i = 0; i < NOBS; ++i) red[i][threadIdx.x] = acc[i];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int i = 0; i < NOBS; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < NOBS) out[(long long)threadIdx.x * a.ly + y] = red[threadIdx.x][0] / a.lx;
+}
+
+// Divide observed row totals by lx.
+__global__ void scale_rows_kernel(double* __restrict__ obs, long long n, double s) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) obs[i] *= s;
+}
+
 static dim3 site_grid(const LatticeArgs& a) {
   return dim3((unsigned)((a.lx + BX - 1) / BX), (unsigned)((a.ly + BY - 1) / BY));
 }
@@ -149,6 +208,27 @@ cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, cons
     else
       step_kernel<LBM_FP32_SHIFTED, false><<<grid, block, 0, s>>>(src, dst, a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_profiles(int prec, const void* src, double* out, const LatticeArgs& a, cudaStream_t s) {
+  if (prec == LBM_FP64)
+    profiles_kernel<LBM_FP64><<<a.ly, 256, 0, s>>>(src, out, a);
+  else
+    profiles_kernel<LBM_FP32_SHIFTED><<<a.ly, 256, 0, s>>>(src, out, a);
+  return cudaGetLastError();
+}
+
+// One float64 step that also adds the row totals of the new state's
+// observables into obs[NOBS][ly] (zeroed here) and scales them to averages.
+cudaError_t launch_step_observe(const void* src, void* dst, const LatticeArgs& a, double* obs, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(obs, 0, sizeof(double) * NOBS * (size_t)a.ly, s);
+  if (e != cudaSuccess) return e;
+  step_kernel<LBM_FP64, true, false, false, true><<<site_grid(a), dim3(BX, BY), 0, s>>>(src, dst, a, obs);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)NOBS * a.ly;
+  scale_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(obs, n, 1.0 / a.lx);
   return cudaGetLastError();
 }
 

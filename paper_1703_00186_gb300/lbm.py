@@ -139,6 +139,19 @@ class Lattice:
         self._check(self.lib.lbm_moments(self.ctx, _ptr(f), *[_ptr(t) for t in out]))
         return tuple(out)
 
+    def profiles(self, f: torch.Tensor | None = None) -> torch.Tensor:
+        """Row averages (8, ly) of rho, u_x, u_y, T, T^2, u_y T, rho|u|^2/2, rho u_y."""
+        out = torch.empty((L.LBM_NOBS, self.ly), dtype=torch.float64, device=self.device)
+        self._check(self.lib.lbm_profiles(self.ctx, _ptr(f), _ptr(out)))
+        return out
+
+    def step_observe(self, n: int, every: int) -> torch.Tensor:
+        """n steps; the row averages after every `every`-th step, (n // every, 8, ly)."""
+        out = torch.empty((max(1, n // every), L.LBM_NOBS, self.ly), dtype=torch.float64, device=self.device)
+        rec = ctypes.c_int(0)
+        self._check(self.lib.lbm_step_observe(self.ctx, int(n), int(every), _ptr(out), ctypes.byref(rec)))
+        return out[:rec.value]
+
     def propagate_bc(self, src: torch.Tensor, dst: torch.Tensor | None = None):
         if dst is None:
             dst = self.new_state()
