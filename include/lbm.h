@@ -96,7 +96,7 @@ enum {
 
 typedef struct lbm_params {
   int32_t lx;         /* physical columns, >= 3 (periodic)                    */
-  int32_t ly;         /* physical rows, >= 6 (walls at both ends)             */
+  int32_t ly;         /* physical rows, 6 <= ly <= 262140 (walls at both ends) */
   int32_t precision;  /* LBM_FP64, LBM_FP32_SHIFTED or LBM_FP64_DF             */
   int32_t flags;      /* LBM_FLAG_* bits                                      */
   double tau;         /* relaxation time, > 0.5 (eq. 1)                        */

@@ -54,8 +54,8 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     std::snprintf(err, errlen, "lattice %d x %d too small (need lx >= 3, ly >= 6)", p.lx, p.ly);
     return LBM_ERR_INVALID;
   }
-  if ((long long)p.lx * (p.ly + 2 * HALO) > (1LL << 40)) {
-    std::snprintf(err, errlen, "lattice too large");
+  if ((long long)p.lx * (p.ly + 2 * HALO) > (1LL << 40) || p.ly > 4 * 65535) {
+    std::snprintf(err, errlen, "lattice too large (ly <= 262140, lx * (ly + 6) <= 2^40)");
     return LBM_ERR_INVALID;
   }
   if (p.precision != LBM_FP64 && p.precision != LBM_FP32_SHIFTED && p.precision != LBM_FP64_DF) {

@@ -72,3 +72,11 @@ def test_regularized_flag_only_with_fp64(lib):
     bad = L.LbmParams(64, 128, L.LBM_FP64, 8, 0.8, 0.0, 1.0, 1.0, 1.0)   # unknown flag bit
     assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(bad), ctypes.c_void_p(8), ctypes.c_void_p(16),
                           lib.lbm_state_bytes(ctypes.byref(bad)), None) == L.LBM_ERR_INVALID
+
+
+def test_oversized_lattices_are_refused(lib):
+    from paper_1703_00186_gb300 import _lib as L
+    ctx = ctypes.c_void_p()
+    tall = L.LbmParams(8, 4 * 65535 + 1, L.LBM_FP64, 0, 0.8, 0.0, 1.0, 1.0, 1.0)
+    assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(tall), ctypes.c_void_p(8), ctypes.c_void_p(16),
+                          lib.lbm_state_bytes(ctypes.byref(tall)), None) == L.LBM_ERR_INVALID

@@ -277,3 +277,63 @@ def test_adjoint_refuses_regularized_context():
     f = lat.new_state(0.1)
     with pytest.raises(LBMError):
         lat.adjoint_step(f, lat.new_cotangent(0.0))
+
+
+# ---------------------------------------------------------------------------
+# Degenerate cases
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64df"])
+def test_uniform_periodic_state_stays_uniform_on_gpu(precision):
+    lx, ly = 40, 20
+    z = np.zeros((ly, lx))
+    lat = Lattice(lx, ly, tau=0.7, g=1e-3, precision=precision, rho0=1.2, periodic_y=True)
+    lat.init(z + 1.3, z + 0.05, z - 0.02, z + 0.9).step(5)
+    s = lat.state().cpu().numpy()[:, 3:-3]
+    for l in range(37):
+        assert np.all(s[l] == s[l, 0, 0]), l
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp64df", 1e-13)])
+def test_rest_equilibrium_is_a_fixed_point_of_the_step_on_gpu(precision, tol):
+    # a uniform fluid at rest without gravity is a fixed point of
+    # propagate + collide (periodic in y: no walls); 3 steps move it by
+    # rounding only: ~1e-16 per step in float64, ~1e-14 per step for the
+    # double-float collide (its equilibrium sums are accurate to ~2^-46)
+    lx, ly = 33, 17
+    z = np.zeros((ly, lx))
+    f = M.init_state(z + 1.25, z, z, z + 0.85)
+    lat = make(M.Params(lx, ly, tau=0.6, g=0.0, periodic_y=True), precision=precision)
+    lat.set_state(to_dev(f))
+    lat.step(3)
+    assert plane_err(lat.state().cpu().numpy(), f) <= tol
+
+
+def test_zero_steps_is_a_no_op():
+    p = M.Params(16, 12, tau=0.8)
+    lat = make(p)
+    f = noisy_state(16, 12, 9)
+    lat.set_state(to_dev(f))
+    lat.step(0)
+    np.testing.assert_array_equal(M.physical(lat.state().cpu().numpy()), M.physical(f))
+
+
+def test_state_larger_than_2_to_31_elements_uses_64_bit_indexing():
+    # 16384 x 4096 float32: 37 * 4102 * 16384 = 2.49e9 elements per state.
+    lx, ly = 16384, 4096
+    rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 8, 3, delta=0.5)
+    rho0 = float(rho.mean())
+    lat = Lattice(lx, ly, tau=0.7, g=1e-4, t_top=tt, t_bottom=tb, precision="fp32", rho0=rho0)
+    assert 37 * (ly + 6) * lx > 2 ** 31
+    lat.init(rho, ux, uy, T).step(1)
+    p = M.Params(lx, ly, tau=0.7, g=1e-4, t_top=tt, t_bottom=tb)
+    state = lat.state()
+    for x0 in (0, lx - 8):   # the last columns of the top rows sit past 2^31
+        pad = 6
+        cols = (x0 - pad + np.arange(8 + 2 * pad)) % lx
+        q = M.Params(len(cols), ly, tau=p.tau, g=p.g, t_top=tt, t_bottom=tb)
+        f = M.init_state(*[np.ascontiguousarray(a[:, cols]) for a in (rho, ux, uy, T)])
+        f[:, 3:-3] = decode32(encode32(f, rho0), rho0)[:, 3:-3]
+        want = M.physical(M.step(f, q))[:, :, pad:pad + 8]
+        got = decode32(state[:, 3:-3, x0:x0 + 8].cpu().numpy(), rho0)
+        scale = np.abs(want).max(axis=(1, 2))
+        assert (np.abs(got - want).max(axis=(1, 2)) / scale).max() <= 2e-6, x0
