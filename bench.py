@@ -148,10 +148,12 @@ def time_steps(lat, k, torch):
 
 
 def dist_max(v, torch, world):
+    """Max of a host scalar over the ranks (the slowest replica sets the time)."""
     if world <= 1:
         return v
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -160,7 +162,8 @@ def barrier(torch, world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
 
 def cpu_baseline(lx, ly, budget_s):
