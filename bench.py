@@ -337,10 +337,23 @@ def batch_study(steps, torch):
     finite = 0
     for i in range(len(b)):
         finite += int(bool(torch.isfinite(b.state(i)[:, 3:-3]).all()))
+    # the same steps as one persistent cooperative launch (bounded grid barrier)
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    b.step_persistent(2)
+    torch.cuda.synchronize()
+    e0.record(s)
+    b.step_persistent(steps)
+    e1.record(s)
+    e1.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    status_p = b.status()
     shapes = Batch.tile_shapes()
     return {"lattices": len(b), "sites": b.sites, "steps": steps, "graph_launches": 1,
             "kernel_launches": steps, "ms": ms, "mlups": b.sites * steps / (ms * 1e-3) / 1e6,
             "tile": shapes[best], "autotune_ms_per_step": {f"{bx}x{by}": t for (bx, by), t in zip(shapes, times)},
+            "persistent": {"ms": ms_p, "mlups": b.sites * steps / (ms_p * 1e-3) / 1e6, "status": status_p,
+                           "what": "one cooperative launch, grid barrier between steps, 32x4 tiles"},
             "lattices_finite_after": finite,
             "state_bytes": 2 * 37 * 4 * sum(sp.lx * (sp.ly + 6) for sp in specs)}
 

@@ -71,6 +71,22 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* best, double* times_ms);
  * of n steps is captured on first use and cached). */
 int lbm_batch_step(lbm_batch* b, int n);
 
+/* Advance every lattice by n >= 0 steps with ONE persistent cooperative
+ * launch: blocks stride over the tile list (32 x 4 tiles) and meet at a grid
+ * barrier between steps.  Every barrier wait is bounded (2 s of global time or
+ * 2^24 polls); if a wait gives up, the kernel sets a status flag and all
+ * blocks return, and lbm_batch_status() reports LBM_ERR_TIMEOUT.  Same
+ * results as lbm_batch_step (the loads use the L2-coherent path because each
+ * step reads what other blocks wrote in the step before). */
+int lbm_batch_step_persistent(lbm_batch* b, int n);
+
+/* Self-test of the bounded wait: launches a two-block kernel whose grid
+ * barrier expects a third block that never comes.  Returns LBM_ERR_TIMEOUT
+ * when the wait gave up after `budget_ms` (1..10000) as designed, LBM_OK if it
+ * did not time out (a failure of the self-test), or another error.  Clears
+ * the barrier state afterwards; the batch stays usable. */
+int lbm_batch_barrier_selftest(lbm_batch* b, int budget_ms);
+
 /* Device pointer of the buffer holding lattice i's current state. */
 void* lbm_batch_current(const lbm_batch* b, int i);
 
@@ -80,7 +96,8 @@ int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy, 
 /* Total physical sites of the batch (sum of lx_i * ly_i). */
 long long lbm_batch_sites(const lbm_batch* b);
 
-/* Synchronise and report the first asynchronous error. */
+/* Synchronise and report the first asynchronous error: a CUDA error
+ * (LBM_ERR_CUDA) or a timed-out persistent-step barrier (LBM_ERR_TIMEOUT). */
 int lbm_batch_status(lbm_batch* b);
 
 #ifdef __cplusplus

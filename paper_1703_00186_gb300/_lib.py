@@ -81,6 +81,8 @@ SIGNATURES = {
     "lbm_batch_set_tile": (c_int, [c_void_p, c_int]),
     "lbm_batch_autotune": (c_int, [c_void_p, c_int, P(c_int), P(c_double)]),
     "lbm_batch_step": (c_int, [c_void_p, c_int]),
+    "lbm_batch_step_persistent": (c_int, [c_void_p, c_int]),
+    "lbm_batch_barrier_selftest": (c_int, [c_void_p, c_int]),
     "lbm_batch_current": (c_void_p, [c_void_p, c_int]),
     "lbm_batch_moments": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_batch_sites": (ctypes.c_longlong, [c_void_p]),

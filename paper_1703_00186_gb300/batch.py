@@ -99,6 +99,15 @@ class Batch:
         self._check(self.lib.lbm_batch_step(self.h, int(n)))
         return self
 
+    def step_persistent(self, n: int = 1):
+        """n steps in one persistent cooperative launch (bounded grid barrier)."""
+        self._check(self.lib.lbm_batch_step_persistent(self.h, int(n)))
+        return self
+
+    def barrier_selftest(self, budget_ms: int = 20) -> int:
+        """Return code of the bounded-wait self-test (LBM_ERR_TIMEOUT expected)."""
+        return self.lib.lbm_batch_barrier_selftest(self.h, int(budget_ms))
+
     def state(self, i) -> torch.Tensor:
         ptr = self.lib.lbm_batch_current(self.h, int(i))
         fa, fb = self.buffers[i]

@@ -8,6 +8,7 @@
 // caller's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -57,15 +58,13 @@ struct BCodec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-template <int PREC, int TBX, int TBY, bool DFARITH = false>
-__global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry* __restrict__ ent,
-                                                               const long long* __restrict__ tile_start,
-                                                               int n, int parity) {
+// One tile of the batch work list; block-wide: every thread of the block
+// calls it (threads outside the lattice skip the work but reach the barriers).
+template <int PREC, int TBX, int TBY, bool DFARITH, bool COHERENT>
+__device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, const long long* __restrict__ tile_start,
+                                           int n, int parity, long long b, LatticeArgs& sa, const void*& s_src,
+                                           void*& s_dst) {
   using T = typename BCodec<PREC>::T;
-  __shared__ __align__(16) LatticeArgs sa;
-  __shared__ const void* s_src;
-  __shared__ void* s_dst;
-  const long long b = blockIdx.x;
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -75,8 +74,8 @@ __global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry*
   {
     static_assert(sizeof(LatticeArgs) % 8 == 0, "LatticeArgs must be a multiple of 8 bytes");
     const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&ent[lo].a);
-    unsigned long long* s = reinterpret_cast<unsigned long long*>(&sa);
-    for (int k = tid; k < (int)(sizeof(LatticeArgs) / 8); k += TBX * TBY) s[k] = __ldg(g + k);
+    unsigned long long* sm = reinterpret_cast<unsigned long long*>(&sa);
+    for (int k = tid; k < (int)(sizeof(LatticeArgs) / 8); k += TBX * TBY) sm[k] = __ldg(g + k);
     if (tid == 0) {
       s_src = ent[lo].f[parity];
       s_dst = ent[lo].f[parity ^ 1];
@@ -89,24 +88,115 @@ __global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry*
   const int ty = (int)(t / tiles_x), tx = (int)(t - (long long)ty * tiles_x);
   const int x = tx * TBX + threadIdx.x;
   const int y = ty * TBY + threadIdx.y;
-  if (x >= a.lx || y >= a.ly) return;
-  const T* __restrict__ src = static_cast<const T*>(s_src);
-  T* __restrict__ dst = static_cast<T*>(s_dst);
-  BCodec<PREC> codec{&a};
-  T f[NPOP];
-  pull(src, x, y, a, f);
-  walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
-  if constexpr (PREC == LBM_FP64 && DFARITH) {
-    __shared__ double s_f[NPOP][TBX * TBY];
-    collide_fp64_df<TBX * TBY>(f, a, s_f, tid, dst, x, y);
-    return;
-  }
-  if constexpr (PREC == LBM_FP64)
-    collide_fp64(f, a);
-  else
-    collide_fp32(f, a);
+  if (x < a.lx && y < a.ly) {
+    const T* __restrict__ src = static_cast<const T*>(s_src);
+    T* __restrict__ dst = static_cast<T*>(s_dst);
+    BCodec<PREC> codec{&a};
+    T f[NPOP];
+    pull<T, COHERENT>(src, x, y, a, f);
+    walls<COHERENT>(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+    if constexpr (PREC == LBM_FP64 && DFARITH) {
+      __shared__ double s_f[NPOP][TBX * TBY];
+      collide_fp64_df<TBX * TBY>(f, a, s_f, tid, dst, x, y);
+    } else {
+      if constexpr (PREC == LBM_FP64)
+        collide_fp64(f, a);
+      else
+        collide_fp32(f, a);
 #pragma unroll
-  for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
+      for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
+    }
+  }
+  __syncthreads();  // sa / s_src / s_dst are reused by the block's next tile
+}
+
+template <int PREC, int TBX, int TBY, bool DFARITH = false>
+__global__ void __launch_bounds__(TBX * TBY) batch_step_kernel(const BatchEntry* __restrict__ ent,
+                                                               const long long* __restrict__ tile_start,
+                                                               int n, int parity) {
+  __shared__ __align__(16) LatticeArgs sa;
+  __shared__ const void* s_src;
+  __shared__ void* s_dst;
+  batch_tile<PREC, TBX, TBY, DFARITH, false>(ent, tile_start, n, parity, blockIdx.x, sa, s_src, s_dst);
+}
+
+// Grid barrier of the persistent kernel with a bounded wait.  State in global
+// memory: arrival count, generation, abort flag, status word.  A block reads
+// the generation, arrives, and (unless it is the last to arrive, which resets
+// the count and advances the generation) waits for the generation to move.
+// The wait gives up after budget_ns of global time or 2^24 polls: the block
+// then sets LBM_STATUS_BARRIER_TIMEOUT in the status word and the abort flag,
+// and every waiting block leaves; the kernel returns instead of hanging.
+struct GridBarrier {
+  unsigned int count, gen, abort, status;
+};
+constexpr unsigned int kBarrierTimeout = 1u;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier(GridBarrier* bar, unsigned int expected, unsigned long long budget_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 1;
+    __threadfence();  // this block's writes before its arrival
+    const unsigned int gen = atomicAdd(&bar->gen, 0u);
+    const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+    if (arrived == expected) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (unsigned int polls = 0;; ++polls) {
+        if (atomicAdd(&bar->gen, 0u) != gen) break;
+        if (atomicAdd(&bar->abort, 0u) != 0u) {
+          ok = 0;
+          break;
+        }
+        if (polls >= (1u << 24) || global_ns() - t0 > budget_ns) {
+          atomicOr(&bar->status, kBarrierTimeout);
+          atomicExch(&bar->abort, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// All `steps` batch steps in one cooperative launch: blocks stride over the
+// tile list, then meet at the grid barrier before the next step reads the
+// populations other blocks have just written (coherent loads).
+template <int PREC, bool DFARITH>
+__global__ void __launch_bounds__(128) batch_persistent_kernel(const BatchEntry* __restrict__ ent,
+                                                               const long long* __restrict__ tile_start, int n,
+                                                               long long tiles, int parity0, int steps,
+                                                               GridBarrier* bar, unsigned long long budget_ns) {
+  __shared__ __align__(16) LatticeArgs sa;
+  __shared__ const void* s_src;
+  __shared__ void* s_dst;
+  for (int st = 0; st < steps; ++st) {
+    const int parity = (parity0 + st) & 1;
+    for (long long b = blockIdx.x; b < tiles; b += gridDim.x)
+      batch_tile<PREC, 32, 4, DFARITH, true>(ent, tile_start, n, parity, b, sa, s_src, s_dst);
+    if (st + 1 < steps && !grid_barrier(bar, gridDim.x, budget_ns)) return;
+  }
+}
+
+// Self-test of the bounded wait: the barrier expects one block more than the
+// grid has, so it can never fill and must time out.
+__global__ void barrier_selftest_kernel(GridBarrier* bar, unsigned long long budget_ns) {
+  grid_barrier(bar, gridDim.x + 1u, budget_ns);
 }
 
 template <int PREC, int I>
@@ -152,6 +242,7 @@ struct lbm_batch {
   int parity;
   long long sites;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (n, parity, tile)
+  GridBarrier* d_bar;  // persistent-kernel barrier state
   char err[512];
 };
 
@@ -187,6 +278,7 @@ void free_batch(lbm_batch* b) {
   for (int t = 0; t < kTiles; ++t)
     if (b->d_tiles[t]) cudaFree(b->d_tiles[t]);
   if (b->d_ent) cudaFree(b->d_ent);
+  if (b->d_bar) cudaFree(b->d_bar);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
 }
@@ -289,6 +381,12 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
       free_batch(b);
       return LBM_ERR_CUDA;
     }
+  }
+  if (cudaMalloc(&b->d_bar, sizeof(GridBarrier)) != cudaSuccess ||
+      cudaMemset(b->d_bar, 0, sizeof(GridBarrier)) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return LBM_ERR_CUDA;
   }
   if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -393,7 +491,77 @@ long long lbm_batch_sites(const lbm_batch* b) { return b ? b->sites : 0; }
 
 int lbm_batch_status(lbm_batch* b) {
   if (!b) return LBM_ERR_INVALID;
-  return bcuda(b, cudaStreamSynchronize(b->stream), "lbm_batch_status");
+  int rc = bcuda(b, cudaStreamSynchronize(b->stream), "lbm_batch_status");
+  if (rc) return rc;
+  GridBarrier h;
+  rc = bcuda(b, cudaMemcpy(&h, b->d_bar, sizeof h, cudaMemcpyDeviceToHost), "lbm_batch_status");
+  if (rc) return rc;
+  if (h.status & kBarrierTimeout) return bfail(b, LBM_ERR_TIMEOUT, "persistent step: grid barrier wait timed out");
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <int PREC, bool DF>
+int launch_persistent(lbm_batch* b, int n, unsigned long long budget_ns) {
+  auto kernel = batch_persistent_kernel<PREC, DF>;
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  int rc = bcuda(b, cudaGetDevice(&dev), "persistent step");
+  if (!rc) rc = bcuda(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "persistent step");
+  if (!rc) rc = bcuda(b, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "persistent step");
+  if (!rc) rc = bcuda(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0), "persistent step");
+  if (rc) return rc;
+  if (!coop || per_sm < 1) return bfail(b, LBM_ERR_INVALID, "persistent step: cooperative launch unavailable");
+  const long long tiles = b->blocks[0];  // the 32 x 4 tiling
+  const unsigned int grid = (unsigned int)std::min<long long>((long long)per_sm * sms, tiles);
+  rc = bcuda(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream), "persistent step");
+  if (rc) return rc;
+  const BatchEntry* ent = b->d_ent;
+  const long long* ts = b->d_tiles[0];
+  int nl = b->n, parity = b->parity, steps = n;
+  GridBarrier* bar = b->d_bar;
+  void* args[] = {(void*)&ent, (void*)&ts, (void*)&nl, (void*)&tiles, (void*)&parity, (void*)&steps, (void*)&bar,
+                  (void*)&budget_ns};
+  return bcuda(b, cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(32, 4), args, 0, b->stream),
+               "persistent step");
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_step_persistent(lbm_batch* b, int n) {
+  if (!b) return LBM_ERR_INVALID;
+  if (n < 0) return bfail(b, LBM_ERR_INVALID, "lbm_batch_step_persistent: n < 0");
+  if (n == 0) return LBM_OK;
+  const unsigned long long budget = 2000000000ull;  // 2 s per barrier wait
+  int rc;
+  if (b->precision == LBM_FP64_DF)
+    rc = launch_persistent<LBM_FP64, true>(b, n, budget);
+  else if (b->precision == LBM_FP64)
+    rc = launch_persistent<LBM_FP64, false>(b, n, budget);
+  else
+    rc = launch_persistent<LBM_FP32_SHIFTED, false>(b, n, budget);
+  if (rc) return rc;
+  b->parity ^= (n & 1);
+  return LBM_OK;
+}
+
+int lbm_batch_barrier_selftest(lbm_batch* b, int budget_ms) {
+  if (!b) return LBM_ERR_INVALID;
+  if (budget_ms < 1 || budget_ms > 10000) return bfail(b, LBM_ERR_INVALID, "budget_ms out of range");
+  int rc = bcuda(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream), "barrier self-test");
+  if (rc) return rc;
+  GridBarrier* bar = b->d_bar;
+  unsigned long long budget = (unsigned long long)budget_ms * 1000000ull;
+  void* args[] = {(void*)&bar, (void*)&budget};
+  rc = bcuda(b, cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(2), dim3(32, 4), args, 0,
+                                            b->stream), "barrier self-test");
+  if (rc) return rc;
+  rc = lbm_batch_status(b);  // LBM_ERR_TIMEOUT when the bounded wait gave up
+  cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream);
+  cudaStreamSynchronize(b->stream);
+  return rc;
 }
 
 }  // extern "C"

@@ -22,7 +22,16 @@ __device__ __forceinline__ long long sidx(const LatticeArgs& a, int l, int y, in
 // propagate (Sect. 2, eq. 1 first term): f_l <- src_l(x - xi_l), periodic in x;
 // in y the source may be a halo row (replaced by the walls) or, in the
 // periodic-y test mode, wraps.
-template <typename T>
+// Loads: read-only path by default; COHERENT = true reads through L2 only
+// (ld.global.cg), for kernels that read what other blocks of the same launch
+// wrote earlier (the persistent batch kernel).
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T load(const T* p) {
+  if constexpr (COHERENT) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <typename T, bool COHERENT = false>
 __device__ __forceinline__ void pull(const T* __restrict__ src, int x, int y,
                                      const LatticeArgs& a, T (&f)[NPOP]) {
 #pragma unroll
@@ -30,7 +39,7 @@ __device__ __forceinline__ void pull(const T* __restrict__ src, int x, int y,
     const int xs = wrap_x(x - vx(l), a.lx);
     int ys = y - vy(l);
     if (a.periodic_y) ys = ys < 0 ? ys + a.ly : (ys >= a.ly ? ys - a.ly : ys);
-    f[l] = __ldg(src + sidx(a, l, ys, xs));
+    f[l] = load<COHERENT>(src + sidx(a, l, ys, xs));
   }
 }
 
@@ -38,7 +47,7 @@ __device__ __forceinline__ void pull(const T* __restrict__ src, int x, int y,
 // in column x, summed in the fixed order: l ascending, then source row
 // ascending; round-to-nearest adds without contraction.  `decode` maps a
 // stored element of population l to its float64 population value.
-template <bool TOP, typename T, typename Decode>
+template <bool TOP, bool COHERENT = false, typename T, typename Decode>
 __device__ __forceinline__ double lost_mass(const T* __restrict__ src, int x,
                                             const LatticeArgs& a, Decode decode) {
   double M = 0.0;
@@ -52,7 +61,7 @@ __device__ __forceinline__ double lost_mass(const T* __restrict__ src, int x,
       const bool lost = TOP ? (e + vy(l) >= 3) : (e + vy(l) < 0);
       if (lost) {
         const int y0 = TOP ? a.ly - 3 + e : e;
-        const double v = decode(l, __ldg(src + sidx(a, l, y0, wrap_x(x - vx(l), a.lx))));
+        const double v = decode(l, load<COHERENT>(src + sidx(a, l, y0, wrap_x(x - vx(l), a.lx))));
         M = first ? v : __dadd_rn(M, v);
         first = false;
       }
@@ -63,18 +72,18 @@ __device__ __forceinline__ double lost_mass(const T* __restrict__ src, int x,
 
 // Replace the unknown slots of a wall row by M(x) q_l (Sect. 2, bc).
 // `encode` maps a float64 population value of population l to storage.
-template <typename S, typename F, typename Decode, typename Encode>
+template <bool COHERENT = false, typename S, typename F, typename Decode, typename Encode>
 __device__ __forceinline__ void walls(const S* __restrict__ src, int x, int y,
                                       const LatticeArgs& a, F (&f)[NPOP],
                                       Decode decode, Encode encode) {
   if (a.periodic_y) return;
   if (y < 3) {
-    const double M = lost_mass<false>(src, x, a, decode);
+    const double M = lost_mass<false, COHERENT>(src, x, a, decode);
 #pragma unroll
     for (int l = 0; l < NPOP; ++l)
       if (vy(l) > 0 && vy(l) > y) f[l] = encode(l, __dmul_rn(M, a.q_bot[l]));
   } else if (y >= a.ly - 3) {
-    const double M = lost_mass<true>(src, x, a, decode);
+    const double M = lost_mass<true, COHERENT>(src, x, a, decode);
     const int d = a.ly - 1 - y;  // row offset from the top wall
 #pragma unroll
     for (int l = 0; l < NPOP; ++l)

@@ -113,3 +113,33 @@ def test_batch_moments():
         got = [t.cpu().numpy() for t in b.moments(i)]
         for g, w in zip(got, want):
             assert np.abs(g - w).max() <= 1e-12 * np.abs(w).max() + 1e-15
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_persistent_launch_matches_graph_launch(precision):
+    specs, flds = build(precision)
+    a = Batch(specs, precision=precision)
+    b = Batch(specs, precision=precision)
+    for i, f in enumerate(flds):
+        a.init(i, *f)
+        b.init(i, *f)
+    a.step(5)
+    b.step_persistent(2).step_persistent(3)
+    assert b.status() == 0
+    for i, s in enumerate(specs):
+        np.testing.assert_array_equal(b.state(i).cpu().numpy()[:, 3:-3], a.state(i).cpu().numpy()[:, 3:-3])
+        if precision == "fp64":
+            assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, flds[i], 5)) <= 1e-12
+
+
+def test_bounded_barrier_wait_times_out_and_batch_stays_usable():
+    from paper_1703_00186_gb300 import _lib as L
+    specs, flds = build("fp64")
+    b = Batch(specs, precision="fp64")
+    assert b.barrier_selftest(20) == L.LBM_ERR_TIMEOUT   # the wait gave up, as designed
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    b.step_persistent(3)
+    assert b.status() == 0
+    for i, s in enumerate(specs):
+        assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, flds[i], 3)) <= 1e-12
