@@ -37,11 +37,15 @@ sys.path.insert(0, ROOT)
 METRIC = "D2Q37 MLUPS, FP64 vs FP32-store, and adjoint/forward step time ratio, 1 GB300"
 WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-5"
 
-# Algorithmic float64 work of the fused step per site (counted from the
-# kernel's formulation; see the design notes): instructions and flops
-# (an FMA counts 2 flops).
-FP64_INSTR_PER_SITE = 377
+# Algorithmic float64 work of the fused step per site, counted from the
+# collide's formulation (an FMA counts 2 flops), and the FP64 instructions per
+# site that ncu measured for the current kernel (profiles/step_kernel_fp64_*).
 FP64_FLOP_PER_SITE = 547
+FP64_INSTR_PER_SITE_NCU = 358
+# DRAM bytes per site of the float64 step (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one 2048 x 1024 launch, 1190.47 MB / 2097152 sites;
+# traffic grows with the site count, so a full launch is scaled by sites).
+FP64_TRAFFIC_BYTES_PER_SITE_NCU = 567.66
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
@@ -574,10 +578,17 @@ def main():
         peak = fp64_peak if fp64_peak else FP64_NOMINAL_TFLOPS
         achieved = FP64_FLOP_PER_SITE * sites / t_launch / 1e12
         res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                           "frac": achieved / peak, "traffic": None,
-                           "peak_source": "measured FP64 FMA probe" if fp64_peak else "nominal 1.25 TF",
-                           "flop_per_site": FP64_FLOP_PER_SITE, "fp64_instr_per_site": FP64_INSTR_PER_SITE,
-                           "hbm_gbs": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9}
+                           "frac": achieved / peak,
+                           "traffic": FP64_TRAFFIC_BYTES_PER_SITE_NCU * sites,
+                           "traffic_source": "ncu 2048x1024 capture scaled by sites "
+                                             "(profiles/step_kernel_fp64_2048x1024.md)",
+                           "peak_source": ("measured FP64 FMA probe (lbm_probe_fma), this run" if fp64_peak
+                                           else "nominal 1.25 TFLOP/s"),
+                           "flop_per_site": FP64_FLOP_PER_SITE, "fp64_instr_per_site_ncu": FP64_INSTR_PER_SITE_NCU,
+                           "fp64_issue_frac": FP64_INSTR_PER_SITE_NCU * sites / t_launch / (peak * 1e12 / 2),
+                           "algorithmic_bytes_per_launch": BYTES_PER_SITE_FP64 * sites,
+                           "hbm_gbs": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9,
+                           "hbm_frac_of_measured": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9 / HBM_GBS_MEASURED}
         res["clocks"] = clocks
     if "fp32" in out:
         f32 = out["fp32"]
@@ -585,6 +596,8 @@ def main():
         res["fp32_store"] = {"mlups": f32["mlups"], "ms_per_step": f32["ms"] / K,
                              "speedup_vs_fp64": (f32["mlups"] / out["fp64"]["mlups"]) if "fp64" in out else None,
                              "hbm_gbs": BYTES_PER_SITE_FP32 * sites / t_launch / 1e9,
+                             "hbm_frac_of_measured": BYTES_PER_SITE_FP32 * sites / t_launch / 1e9 / HBM_GBS_MEASURED,
+                             "hbm_peak_source": HBM_PEAK_SOURCE,
                              "finite_after_timed_steps": f32["finite"]}
     if "fp64df" in out:
         d = out["fp64df"]
