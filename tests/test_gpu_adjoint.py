@@ -100,3 +100,18 @@ def test_init_vjp_parity():
     got = [t.cpu().numpy() for t in lat.init_vjp(rho, ux, uy, T, to_dev(lam))]
     for g, w in zip(got, want):
         assert np.abs(g - w).max() <= 1e-12 * np.abs(w).max()
+
+
+def test_moments_vjp_fp32_state_parity():
+    lx, ly = 21, 9
+    rho0 = 1.05
+    p = M.Params(lx, ly, tau=0.8)
+    f = noisy_state(lx, ly, 62)
+    d = (f - K["w"][:, None, None] * rho0).astype(np.float32)
+    fdec = d.astype(np.float64) + K["w"][:, None, None] * rho0
+    rng = np.random.default_rng(63)
+    g = [rng.standard_normal((ly, lx)) for _ in range(4)]
+    want = A.moments_vjp(fdec, *g)
+    lat = make(p, precision="fp32", rho0=rho0)
+    got = lat.moments_vjp(to_dev(d, torch.float32), *g).cpu().numpy()
+    assert plane_err(got, want) <= 1e-12

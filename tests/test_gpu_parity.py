@@ -337,3 +337,37 @@ def test_state_larger_than_2_to_31_elements_uses_64_bit_indexing():
         got = decode32(state[:, 3:-3, x0:x0 + 8].cpu().numpy(), rho0)
         scale = np.abs(want).max(axis=(1, 2))
         assert (np.abs(got - want).max(axis=(1, 2)) / scale).max() <= 2e-6, x0
+
+
+# ---------------------------------------------------------------------------
+# Boundary paths: checkpoint through pinned host memory, explicit-buffer step
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_round_trip_through_pinned_host_memory(precision):
+    lx, ly = 50, 22
+    rho, ux, uy, T = synth.random_fields(lx, ly, 11)
+    lat = Lattice(lx, ly, tau=0.7, g=1e-3, t_top=0.9, t_bottom=1.1, precision=precision, rho0=1.1)
+    lat.init(rho, ux, uy, T).step(3)
+    host = torch.empty(lat.shape, dtype=lat.dtype, pin_memory=True)
+    lat.get_state(host)
+    torch.cuda.synchronize()
+    ref = lat.state().clone()
+    lat.step(4)                       # move on, then restore the checkpoint
+    lat.set_state(host)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lat.state()[:, 3:-3].cpu().numpy(), ref[:, 3:-3].cpu().numpy())
+    lat.step(4)
+    again = lat.state().clone()
+    lat.set_state(host).step(4)
+    np.testing.assert_array_equal(lat.state()[:, 3:-3].cpu().numpy(), again[:, 3:-3].cpu().numpy())
+
+
+def test_step_from_equals_step():
+    lx, ly = 41, 19
+    rho, ux, uy, T = synth.random_fields(lx, ly, 12)
+    lat = Lattice(lx, ly, tau=0.7, g=1e-3, t_top=0.9, t_bottom=1.1).init(rho, ux, uy, T)
+    src = lat.state().clone()
+    dst = lat.new_state()
+    lat.step_from(src, dst)
+    lat.step(1)
+    np.testing.assert_array_equal(dst[:, 3:-3].cpu().numpy(), lat.state()[:, 3:-3].cpu().numpy())
