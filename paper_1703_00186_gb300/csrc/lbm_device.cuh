@@ -225,49 +225,80 @@ __device__ __forceinline__ MomentsDF moment_sums_df(const float (&d)[NPOP]) {
 // lattice) are still summed, only no longer exactly.
 struct SplitAcc {
   float h, l;
-  int m;
+  unsigned m;  // integer part, accumulated modulo 2^32 (the true sum fits in int32)
 };
 
 __device__ __forceinline__ DF split_result(const SplitAcc& a) {
   // m * 2^-34 as two exact floats, then h + m + l in double-float
-  const float m_hi = (float)(a.m >> 12) * 0x1p-22f;
-  const float m_lo = (float)(a.m & 0xfff) * 0x1p-34f;
+  const int m = (int)a.m;
+  const float m_hi = (float)(m >> 12) * 0x1p-22f;
+  const float m_lo = (float)(m & 0xfff) * 0x1p-34f;
   DF r = df_two_sum(a.h, m_hi);
   r = df_add(r, m_lo);
   return df_add(r, a.l);
 }
 
+// Three-level split of one float32 value v (|v| < 2^10):
+//   v = h + m 2^-34 + lo,  h on the 2^-12 grid, m an integer with
+//   |m| <= 2^21, |lo| <= 2^-35.
+// h = (v + C1) - C1 rounds v to the 2^-12 grid; rem = v - h is exact and
+// |rem| <= 2^-13, so t = rem + C2 lies in [2^-11, 2^-10), where the float
+// spacing is 2^-34: the bit pattern of t minus that of C2 is round(rem 2^34).
+// The pattern itself is returned (bits = m + K2); the constant K2 cancels in
+// the differences of a +-pair and is removed once from the other sums.
+struct Split {
+  float h, lo;
+  unsigned bits;
+};
+
+__device__ __forceinline__ Split split3(float v) {
+  constexpr float C1 = 3072.0f;     // 1.5 * 2^11: grid 2^-12
+  constexpr float C2 = 0x1.8p-11f;  // 1.5 * 2^-11: grid 2^-34
+  const float h = (v + C1) - C1;
+  const float rem = v - h;
+  const float t = rem + C2;
+  return {h, rem - (t - C2), __float_as_uint(t)};
+}
+
+// Exact (to < 2^-50 relative) float32 sums sum_l d_l, sum_l xi_l d_l and
+// sum_l |xi_l|^2 d_l: h parts sum exactly on the 2^-12 grid (float, exact
+// while sum_l |xi_l|^2 |d_l| < 2^12; deviations are O(1) at most), the
+// 2^-34-grid parts exactly as integers, and only the tiny lo parts round.
+// Population pairs (2k+1, 2k+2) = (R_k, -R_k) are combined first: the even
+// moments take d+ + d-, the odd ones d+ - d-.
 __device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
-  constexpr float C1 = 3072.0f;        // 1.5 * 2^11: grid 2^-12
-  constexpr float C2 = 0x1.8p-11f;     // 1.5 * 2^-11: grid 2^-34
-  const int K2 = __float_as_int(C2);
-  SplitAcc r{0.f, 0.f, 0}, jx{0.f, 0.f, 0}, jy{0.f, 0.f, 0}, e{0.f, 0.f, 0};
+  constexpr unsigned K2 = 0x3a400000u;  // bit pattern of 1.5 * 2^-11
+  const Split s0 = split3(d[0]);
+  SplitAcc r{s0.h, s0.lo, s0.bits}, jx{0.f, 0.f, 0u}, jy{0.f, 0.f, 0u}, e{0.f, 0.f, 0u};
+  unsigned e_off = 0u;
 #pragma unroll
-  for (int l = 0; l < NPOP; ++l) {
-    const float h = (d[l] + C1) - C1;
-    const float rem = d[l] - h;
-    const float t = rem + C2;
-    const int m = __float_as_int(t) - K2;
-    const float lo = rem - (t - C2);
-    r.h += h;
-    r.m += m;
-    r.l += lo;
-    if (vx(l) != 0) {
-      jx.h = fmaf((float)vx(l), h, jx.h);
-      jx.m += vx(l) * m;
-      jx.l = fmaf((float)vx(l), lo, jx.l);
+  for (int k = 0; k < NPAIR; ++k) {
+    const Split p = split3(d[2 * k + 1]);
+    const Split q = split3(d[2 * k + 2]);
+    const float sh = p.h + q.h, dh = p.h - q.h;      // exact: 2^-12 grid, < 2^12
+    const unsigned sm = p.bits + q.bits, dm = p.bits - q.bits;
+    const float sl = p.lo + q.lo, dl = p.lo - q.lo;
+    const int c2 = rep_x(k) * rep_x(k) + rep_y(k) * rep_y(k);
+    r.h += sh;
+    r.m += sm;
+    r.l += sl;
+    e.h = fmaf((float)c2, sh, e.h);
+    e.m += (unsigned)c2 * sm;
+    e.l = fmaf((float)c2, sl, e.l);
+    e_off += 2u * (unsigned)c2;
+    if (rep_x(k) != 0) {
+      jx.h = fmaf((float)rep_x(k), dh, jx.h);
+      jx.m += (unsigned)rep_x(k) * dm;
+      jx.l = fmaf((float)rep_x(k), dl, jx.l);
     }
-    if (vy(l) != 0) {
-      jy.h = fmaf((float)vy(l), h, jy.h);
-      jy.m += vy(l) * m;
-      jy.l = fmaf((float)vy(l), lo, jy.l);
-    }
-    if (sq(l) != 0) {
-      e.h = fmaf((float)sq(l), h, e.h);
-      e.m += sq(l) * m;
-      e.l = fmaf((float)sq(l), lo, e.l);
+    if (rep_y(k) != 0) {
+      jy.h = fmaf((float)rep_y(k), dh, jy.h);
+      jy.m += (unsigned)rep_y(k) * dm;
+      jy.l = fmaf((float)rep_y(k), dl, jy.l);
     }
   }
+  r.m -= (unsigned)NPOP * K2;
+  e.m -= e_off * K2;
   return {split_result(r), split_result(jx), split_result(jy), split_result(e)};
 }
 
@@ -336,42 +367,49 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 
 // BGK collide on float32 deviations d_l = f_l - w_l rho0 (FP32 shifted storage):
 //   d_l <- (1 - omega) d_l + omega (f^eq_l - w_l rho0).
-// The moment sums, the velocity, the temperature and the temperature-dependent
-// equilibrium coefficients are carried in double-float (about 48 bits, on the
-// FP32 pipe; GB300 issues FP64 at 1/64 of the FP32 rate); the per-population
-// polynomial and the relaxation are float32.  Rounding the per-shell
-// coefficients to float32 leaves the discrete equilibrium's mass, momentum and
-// energy off by ~1e-8 relative in a way that repeats from step to step and so
-// accumulates; after the relaxation the conserved moments of the new
-// populations are therefore measured in double-float and the small defect is
-// put back on the rest and |xi| = 1 populations, so the collide conserves mass
-// and energy and adds exactly rho g to the momentum.
+// Precision plan (GB300 issues FP64 at 1/64 of the FP32 rate, so nothing here
+// uses the FP64 pipe):
+//  * the moment sums are exact (moment_sums_split, error < 2^-50);
+//  * the quantities that carry cancellation are double-float (about 48
+//    bits): rho, 1/rho, E, T, theta = T' - 1 and rho (B00 - 1), i.e. the
+//    temperature-dependent zeroth-order part of the equilibrium;
+//  * u, |u'|^2 and the coefficients of the cu-dependent terms (which are
+//    scaled by cu or cu^2) are float32, as are the per-population polynomial
+//    and the relaxation.
+// Rounding the per-shell coefficients to float32 leaves the discrete
+// equilibrium's mass, momentum and energy off by ~1e-8 relative in a way that
+// repeats from step to step and so accumulates; after the relaxation the
+// conserved moments of the new populations are therefore measured exactly and
+// the small defect is put back on the rest and |xi| = 1 populations, so the
+// collide conserves mass and energy and adds exactly rho g to the momentum.
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
   const MomentsDF dev = moment_sums_split(d);
   const DF rho = df_add(dev.rho, dfc(a.df_rho0));
   const DF inv = df_rcp(rho);
-  const DF ux = df_mul(dev.Jx, inv), uy = df_mul(dev.Jy, inv);
+  const float invf = inv.hi;
+  const float ux = dev.Jx.hi * invf, uy = dev.Jy.hi * invf;          // xi units
+  const float usq = fmaf(ux, ux, uy * uy);
   const DF exi = df_add(dev.Exi, dfc(a.df_e0));
-  const DF usq = df_add(df_mul(ux, ux), df_mul(uy, uy));
-  const DF T = df_mul(df_sub(df_mul(exi, inv), usq), dfc(a.df_half_r2));
+  const DF T = df_mul(df_add(df_mul(exi, inv), -usq), dfc(a.df_half_r2));
   const DF theta = df_add(T, dfc(a.df_tshift));
-  const DF uys = df_sub(uy, dfc(a.df_taug_r));
-  const DF U2 = df_mul(df_add(df_mul(ux, ux), df_mul(uys, uys)), dfc(a.df_r2));
-  // equilibrium coefficients (see eq_coef), double-float
-  const DF th2 = df_mul(theta, theta);
-  const DF B20 = df_add(df_add(df_mul(U2, -0.25f), df_mul(theta, -1.5f)), 0.5f);
-  const DF B10 = df_add(df_add(df_scale2(U2, -0.5f), df_scale2(theta, -2.0f)), 1.0f);
-  const DF B00 = df_add(df_add(df_mul(U2, df_add(df_scale2(U2, 0.125f), -0.5f)),
-                               df_mul(theta, df_add(df_add(U2, -1.0f), theta))), 1.0f);
-  const DF B01 = df_mul(theta, df_sub(df_add(df_scale2(U2, -0.25f), 0.5f), theta));
-  const DF B02 = df_scale2(th2, 0.125f);
-  // hand-over to float32
-  const float v_x = df_mul(ux, dfc(a.df_r2)).hi, v_y = df_mul(uys, dfc(a.df_r2)).hi;
-  const float b10 = B10.hi, b11 = 0.5f * theta.hi, b20 = B20.hi, b21 = 0.25f * theta.hi;
-  const float rb00 = df_sub(df_mul(rho, B00), dfc(a.df_rho0)).hi;  // rho B00 - rho0
-  const float rb01 = df_mul(rho, B01).hi, rb02 = df_mul(rho, B02).hi;
+  const float th = theta.hi;
+  const float r2f = a.df_r2[0];
+  const float uys = uy - a.df_taug_r[0];
+  const float U2 = r2f * fmaf(ux, ux, uys * uys);
+  // equilibrium coefficients (see eq_coef); B00 - 1 in double-float
+  const DF b00m1 = df_add(df_mul(theta, df_add(theta, U2 - 1.0f)), U2 * fmaf(0.125f, U2, -0.5f));
+  const float b20 = fmaf(-1.5f, th, fmaf(-0.25f, U2, 0.5f));
+  const float b21 = 0.25f * th;
+  const float b10 = fmaf(-2.0f, th, fmaf(-0.5f, U2, 1.0f));
+  const float b11 = 0.5f * th;
+  const float b01 = th * (fmaf(-0.25f, U2, 0.5f) - th);
+  const float b02 = 0.125f * th * th;
+  const float rf = rho.hi;
+  const float v_x = r2f * ux, v_y = r2f * uys;
+  const float rb00 = df_add(df_mul(rho, b00m1), dev.rho).hi;  // rho B00 - rho0 = (rho - rho0) + rho (B00 - 1)
+  const float rb01 = rf * b01, rb02 = rf * b02;
   const float om = a.omega_f, omc = a.omc_f;
-  const float wr = df_mul(rho, dfc(a.df_omega)).hi;
+  const float wr = om * rf;
   d[0] = fmaf(omc, d[0], om * a.w_shell_f[0] * rb00);
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
@@ -391,16 +429,17 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
   }
   // conserved-moment correction.  Targets of the exact BGK update with the
   // equilibrium shift (omega tau = 1), deviation form, xi units, g_xi = g / r:
-  //   mass and Jx unchanged, Jy - rho g_xi, Exi - 2 g_xi Jy + rho g_xi^2.
+  //   mass and Jx unchanged, Jy - rho g_xi, Exi - 2 g_xi Jy + rho g_xi^2
+  // (the gravity terms are ~1e-5 of the sums, float32 is enough for them).
   const MomentsDF nw = moment_sums_split(d);
-  const DF gr = dfc(a.df_g_r);
-  const DF rg = df_mul(rho, gr);
-  const DF tjy = df_sub(dev.Jy, rg);
-  const DF te = df_add(df_sub(dev.Exi, df_scale2(df_mul(dev.Jy, gr), 2.0f)), df_mul(rg, gr));
-  const float dm = df_sub(nw.rho, dev.rho).hi;
-  const float djx = df_sub(nw.Jx, dev.Jx).hi;
-  const float djy = df_sub(nw.Jy, tjy).hi;
-  const float de = df_sub(nw.Exi, te).hi;
+  const float gr = a.df_g_r[0];
+  const DF tjy = df_add(dev.Jy, -rf * gr);
+  const DF te = df_add(dev.Exi, fmaf(rf * gr, gr, -2.0f * gr * dev.Jy.hi));
+  // defects: the two sums agree to ~1e-8, so hi - hi is exact (Sterbenz)
+  const float dm = (nw.rho.hi - dev.rho.hi) + (nw.rho.lo - dev.rho.lo);
+  const float djx = (nw.Jx.hi - dev.Jx.hi) + (nw.Jx.lo - dev.Jx.lo);
+  const float djy = (nw.Jy.hi - tjy.hi) + (nw.Jy.lo - tjy.lo);
+  const float de = (nw.Exi.hi - te.hi) + (nw.Exi.lo - te.lo);
   d[0] += de - dm;
   d[1] += (-0.5f * de - djx) * 0.5f;  // xi = (1, 0)
   d[2] += (-0.5f * de + djx) * 0.5f;  // xi = (-1, 0)
