@@ -224,77 +224,70 @@ __device__ __forceinline__ MomentsDF moment_sums_df(const float (&d)[NPOP]) {
 // The result is returned as double-float.  Values with |d| >= 4 (a diverged
 // lattice) are still summed, only no longer exactly.
 struct SplitAcc {
-  float h, l;
+  float h;
   unsigned m;  // integer part, accumulated modulo 2^32 (the true sum fits in int32)
 };
 
 __device__ __forceinline__ DF split_result(const SplitAcc& a) {
-  // m * 2^-34 as two exact floats, then h + m + l in double-float
+  // h + m 2^-34 in double-float (m 2^-34 as two exact floats)
   const int m = (int)a.m;
   const float m_hi = (float)(m >> 12) * 0x1p-22f;
   const float m_lo = (float)(m & 0xfff) * 0x1p-34f;
-  DF r = df_two_sum(a.h, m_hi);
-  r = df_add(r, m_lo);
-  return df_add(r, a.l);
+  return df_add(df_two_sum(a.h, m_hi), m_lo);
 }
 
-// Three-level split of one float32 value v (|v| < 2^10):
-//   v = h + m 2^-34 + lo,  h on the 2^-12 grid, m an integer with
-//   |m| <= 2^21, |lo| <= 2^-35.
+// Two-level split of one float32 value v (|v| < 2^10):
+//   v = h + m 2^-34 + e,  h on the 2^-12 grid, m an integer with
+//   |m| <= 2^21, |e| <= 2^-35 (e is dropped).
 // h = (v + C1) - C1 rounds v to the 2^-12 grid; rem = v - h is exact and
 // |rem| <= 2^-13, so t = rem + C2 lies in [2^-11, 2^-10), where the float
 // spacing is 2^-34: the bit pattern of t minus that of C2 is round(rem 2^34).
 // The pattern itself is returned (bits = m + K2); the constant K2 cancels in
 // the differences of a +-pair and is removed once from the other sums.
 struct Split {
-  float h, lo;
+  float h;
   unsigned bits;
 };
 
-__device__ __forceinline__ Split split3(float v) {
+__device__ __forceinline__ Split split2(float v) {
   constexpr float C1 = 3072.0f;     // 1.5 * 2^11: grid 2^-12
   constexpr float C2 = 0x1.8p-11f;  // 1.5 * 2^-11: grid 2^-34
   const float h = (v + C1) - C1;
-  const float rem = v - h;
-  const float t = rem + C2;
-  return {h, rem - (t - C2), __float_as_uint(t)};
+  return {h, __float_as_uint((v - h) + C2)};
 }
 
-// Exact (to < 2^-50 relative) float32 sums sum_l d_l, sum_l xi_l d_l and
-// sum_l |xi_l|^2 d_l: h parts sum exactly on the 2^-12 grid (float, exact
-// while sum_l |xi_l|^2 |d_l| < 2^12; deviations are O(1) at most), the
-// 2^-34-grid parts exactly as integers, and only the tiny lo parts round.
-// Population pairs (2k+1, 2k+2) = (R_k, -R_k) are combined first: the even
-// moments take d+ + d-, the odd ones d+ - d-.
+// Float32 sums sum_l d_l, sum_l xi_l d_l and sum_l |xi_l|^2 d_l of the exact
+// values h_l + m_l 2^-34: the h parts sum exactly on the 2^-12 grid (float,
+// exact while sum_l |xi_l|^2 |d_l| < 2^12; deviations are O(1) at most) and
+// the 2^-34-grid parts exactly as integers.  The only error is the rounding
+// of each d_l to the 2^-34 grid: at most 2^-35 per term, round-to-nearest and
+// so without bias, three orders of magnitude below the float32 quantum of the
+// stored deviations.  Population pairs (2k+1, 2k+2) = (R_k, -R_k) are
+// combined first: the even moments take d+ + d-, the odd ones d+ - d-.
 __device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
   constexpr unsigned K2 = 0x3a400000u;  // bit pattern of 1.5 * 2^-11
-  const Split s0 = split3(d[0]);
-  SplitAcc r{s0.h, s0.lo, s0.bits}, jx{0.f, 0.f, 0u}, jy{0.f, 0.f, 0u}, e{0.f, 0.f, 0u};
+  const Split s0 = split2(d[0]);
+  SplitAcc r{s0.h, s0.bits}, jx{0.f, 0u}, jy{0.f, 0u}, e{0.f, 0u};
   unsigned e_off = 0u;
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
-    const Split p = split3(d[2 * k + 1]);
-    const Split q = split3(d[2 * k + 2]);
+    const Split p = split2(d[2 * k + 1]);
+    const Split q = split2(d[2 * k + 2]);
     const float sh = p.h + q.h, dh = p.h - q.h;      // exact: 2^-12 grid, < 2^12
     const unsigned sm = p.bits + q.bits, dm = p.bits - q.bits;
-    const float sl = p.lo + q.lo, dl = p.lo - q.lo;
     const int c2 = rep_x(k) * rep_x(k) + rep_y(k) * rep_y(k);
     r.h += sh;
     r.m += sm;
-    r.l += sl;
     e.h = fmaf((float)c2, sh, e.h);
     e.m += (unsigned)c2 * sm;
-    e.l = fmaf((float)c2, sl, e.l);
     e_off += 2u * (unsigned)c2;
     if (rep_x(k) != 0) {
       jx.h = fmaf((float)rep_x(k), dh, jx.h);
       jx.m += (unsigned)rep_x(k) * dm;
-      jx.l = fmaf((float)rep_x(k), dl, jx.l);
     }
     if (rep_y(k) != 0) {
       jy.h = fmaf((float)rep_y(k), dh, jy.h);
       jy.m += (unsigned)rep_y(k) * dm;
-      jy.l = fmaf((float)rep_y(k), dl, jy.l);
     }
   }
   r.m -= (unsigned)NPOP * K2;
@@ -369,7 +362,7 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 //   d_l <- (1 - omega) d_l + omega (f^eq_l - w_l rho0).
 // Precision plan (GB300 issues FP64 at 1/64 of the FP32 rate, so nothing here
 // uses the FP64 pipe):
-//  * the moment sums are exact (moment_sums_split, error < 2^-50);
+//  * the moment sums are accurate to 2^-35 per term (moment_sums_split);
 //  * the quantities that carry cancellation are double-float (about 48
 //    bits): rho, 1/rho, E, T, theta = T' - 1 and rho (B00 - 1), i.e. the
 //    temperature-dependent zeroth-order part of the equilibrium;
@@ -379,7 +372,7 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 // Rounding the per-shell coefficients to float32 leaves the discrete
 // equilibrium's mass, momentum and energy off by ~1e-8 relative in a way that
 // repeats from step to step and so accumulates; after the relaxation the
-// conserved moments of the new populations are therefore measured exactly and
+// conserved moments of the new populations are therefore measured again and
 // the small defect is put back on the rest and |xi| = 1 populations, so the
 // collide conserves mass and energy and adds exactly rho g to the momentum.
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
