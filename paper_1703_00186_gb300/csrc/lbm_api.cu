@@ -81,6 +81,13 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->lx = p.lx;
   a->ly = p.ly;
   a->plane = (long long)(p.ly + 2 * HALO) * p.lx;
+  a->idx32 = (long long)NPOP * a->plane < (1LL << 31) ? 1 : 0;
+  if (a->idx32) {
+    for (int l = 0; l < NPOP; ++l) {
+      a->plane_off[l] = (int)(l * a->plane);
+      a->pull_off[l] = (int)(l * a->plane - (long long)vy(l) * p.lx - vx(l));
+    }
+  }
   a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;
   a->regularized = (p.flags & LBM_FLAG_REGULARIZED) ? 1 : 0;
   a->tau = p.tau;

@@ -43,6 +43,39 @@ __device__ __forceinline__ void pull(const T* __restrict__ src, int x, int y,
   }
 }
 
+// Element offset of site (y, x) within a population plane.
+__device__ __forceinline__ int site_off(const LatticeArgs& a, int y, int x) { return (y + HALO) * a.lx + x; }
+
+// True where the pull of every population is a fixed site-relative offset:
+// 32-bit state indices, a column at least 3 sites from the periodic seam, and
+// walls (not the periodic-y test mode) in y.
+__device__ __forceinline__ bool fast_site(const LatticeArgs& a, int x) {
+  return a.idx32 && !a.periodic_y && x >= 3 && x < a.lx - 3;
+}
+
+// pull at a fast site: one address computation per population.
+template <typename T, bool COHERENT = false>
+__device__ __forceinline__ void pull_fast(const T* __restrict__ src, int site, const LatticeArgs& a,
+                                          T (&f)[NPOP]) {
+  const T* s = src + site;
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) f[l] = load<COHERENT>(s + a.pull_off[l]);
+}
+
+// Store the 37 populations of a site (any site, fast indices if idx32).
+template <typename T>
+__device__ __forceinline__ void store_site(T* __restrict__ dst, int x, int y, const LatticeArgs& a,
+                                           const T (&f)[NPOP]) {
+  if (a.idx32) {
+    T* d = dst + site_off(a, y, x);
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) d[a.plane_off[l]] = f[l];
+  } else {
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
+  }
+}
+
 // Mass M(x) that left through the bottom (top) wall during propagate and lands
 // in column x, summed in the fixed order: l ascending, then source row
 // ascending; round-to-nearest adds without contraction.  `decode` maps a

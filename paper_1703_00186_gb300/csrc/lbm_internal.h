@@ -106,6 +106,12 @@ struct LatticeArgs {
   double ginv[63];        // inverse Gram blocks EE(36) OE(9) EO(9) OO(9)
   float df_c2_shell[NSHELL][2];
   unsigned int* status;  // device status word
+  // Site-relative element offsets for states of fewer than 2^31 elements
+  // (idx32 != 0): the pull source of population l of an interior column is
+  // site + pull_off[l], its destination site + plane_off[l].
+  int idx32;
+  int pull_off[NPOP];    // l plane - xi_ly lx - xi_lx
+  int plane_off[NPOP];   // l plane
 };
 
 }  // namespace lbm

@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
   T* __restrict__ dst = static_cast<T*>(dst_);
   Codec<PREC> codec{&a};
   T f[NPOP];
-  pull(src, x, y, a, f);
+  if (fast_site(a, x)) pull_fast(src, site_off(a, y, x), a, f);
+  else pull(src, x, y, a, f);
   walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
   if constexpr (PREC == LBM_FP64 && DFARITH) {
     if (COLLIDE) {
@@ -85,8 +86,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
       collide_fp32(f, a);
     }
   }
-#pragma unroll
-  for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
+  store_site(dst, x, y, a, f);
 }
 
 template <int PREC>
