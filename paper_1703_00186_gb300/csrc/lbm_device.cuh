@@ -409,68 +409,81 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 // the small defect is put back on the rest and |xi| = 1 populations, so the
 // collide conserves mass and energy and adds exactly rho g to the momentum.
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
-  const MomentsDF dev = moment_sums_split(d);
-  const DF rho = df_add(dev.rho, dfc(a.df_rho0));
-  const DF inv = df_rcp(rho);
-  const float invf = inv.hi;
-  const float ux = dev.Jx.hi * invf, uy = dev.Jy.hi * invf;          // xi units
-  const float usq = fmaf(ux, ux, uy * uy);
-  const DF exi = df_add(dev.Exi, dfc(a.df_e0));
-  const DF T = df_mul(df_add(df_mul(exi, inv), -usq), dfc(a.df_half_r2));
-  const DF theta = df_add(T, dfc(a.df_tshift));
-  const float th = theta.hi;
-  const float r2f = a.df_r2[0];
-  const float uys = uy - a.df_taug_r[0];
-  const float U2 = r2f * fmaf(ux, ux, uys * uys);
-  // equilibrium coefficients (see eq_coef); B00 - 1 in double-float
-  const DF b00m1 = df_add(df_mul(theta, df_add(theta, U2 - 1.0f)), U2 * fmaf(0.125f, U2, -0.5f));
-  const float b20 = fmaf(-1.5f, th, fmaf(-0.25f, U2, 0.5f));
-  const float b21 = 0.25f * th;
-  const float b10 = fmaf(-2.0f, th, fmaf(-0.5f, U2, 1.0f));
-  const float b11 = 0.5f * th;
-  const float b01 = th * (fmaf(-0.25f, U2, 0.5f) - th);
-  const float b02 = 0.125f * th * th;
-  const float rf = rho.hi;
-  const float v_x = r2f * ux, v_y = r2f * uys;
-  const float rb00 = df_add(df_mul(rho, b00m1), dev.rho).hi;  // rho B00 - rho0 = (rho - rho0) + rho (B00 - 1)
-  const float rb01 = rf * b01, rb02 = rf * b02;
-  const float om = a.omega_f, omc = a.omc_f;
-  const float wr = om * rf;
-  d[0] = fmaf(omc, d[0], om * a.w_shell_f[0] * rb00);
+  MomentsDF dev;
+  float rf = 0.f;
+  // Both passes share one copy of the moment-sum code (a rolled loop of two
+  // iterations): the kernel is instruction-issue bound and a smaller body
+  // keeps it in the instruction cache.
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const MomentsDF m = moment_sums_split(d);
+    if (pass == 0) {
+      dev = m;
+      const DF rho = df_add(dev.rho, dfc(a.df_rho0));
+      const DF inv = df_rcp(rho);
+      const float invf = inv.hi;
+      const float ux = dev.Jx.hi * invf, uy = dev.Jy.hi * invf;  // xi units
+      const float usq = fmaf(ux, ux, uy * uy);
+      const DF exi = df_add(dev.Exi, dfc(a.df_e0));
+      const DF T = df_mul(df_add(df_mul(exi, inv), -usq), dfc(a.df_half_r2));
+      const DF theta = df_add(T, dfc(a.df_tshift));
+      const float th = theta.hi;
+      const float r2f = a.df_r2[0];
+      const float uys = uy - a.df_taug_r[0];
+      const float U2 = r2f * fmaf(ux, ux, uys * uys);
+      // equilibrium coefficients (see eq_coef); B00 - 1 in double-float
+      const DF b00m1 = df_add(df_mul(theta, df_add(theta, U2 - 1.0f)), U2 * fmaf(0.125f, U2, -0.5f));
+      const float b20 = fmaf(-1.5f, th, fmaf(-0.25f, U2, 0.5f));
+      const float b21 = 0.25f * th;
+      const float b10 = fmaf(-2.0f, th, fmaf(-0.5f, U2, 1.0f));
+      const float b11 = 0.5f * th;
+      const float b01 = th * (fmaf(-0.25f, U2, 0.5f) - th);
+      const float b02 = 0.125f * th * th;
+      rf = rho.hi;
+      const float v_x = r2f * ux, v_y = r2f * uys;
+      const float rb00 = df_add(df_mul(rho, b00m1), dev.rho).hi;  // rho B00 - rho0 = (rho - rho0) + rho (B00 - 1)
+      const float rb01 = rf * b01, rb02 = rf * b02;
+      const float om = a.omega_f, omc = a.omc_f;
+      const float wr = om * rf;
+      d[0] = fmaf(omc, d[0], om * a.w_shell_f[0] * rb00);
 #pragma unroll
-  for (int k = 0; k < NPAIR; ++k) {
-    const int j = pair_shell(k);
-    const float c2 = a.c2_shell_f[j];
-    const float w = a.w_shell_f[j];
-    const float A1 = fmaf(b11, c2, b10);
-    const float A2 = fmaf(b21, c2, b20);
-    const float alpha = wr * w;                                        // omega w rho
-    const float beta = om * w * fmaf(c2, fmaf(c2, rb02, rb01), rb00);  // omega w (rho A0 - rho0)
-    const float cu = pair_cu<float>(k, v_x, v_y);
-    const float cu2 = cu * cu;
-    const float E = fmaf(alpha * cu2, fmaf(cu2, 1.0f / 24.0f, A2), beta);
-    const float O = alpha * cu * fmaf(cu2, 1.0f / 6.0f, A1);
-    d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
-    d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
+      for (int k = 0; k < NPAIR; ++k) {
+        const int j = pair_shell(k);
+        const float c2 = a.c2_shell_f[j];
+        const float w = a.w_shell_f[j];
+        const float A1 = fmaf(b11, c2, b10);
+        const float A2 = fmaf(b21, c2, b20);
+        const float alpha = wr * w;                                        // omega w rho
+        const float beta = om * w * fmaf(c2, fmaf(c2, rb02, rb01), rb00);  // omega w (rho A0 - rho0)
+        const float cu = pair_cu<float>(k, v_x, v_y);
+        const float cu2 = cu * cu;
+        const float E = fmaf(alpha * cu2, fmaf(cu2, 1.0f / 24.0f, A2), beta);
+        const float O = alpha * cu * fmaf(cu2, 1.0f / 6.0f, A1);
+        d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
+        d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
+      }
+    } else {
+      // conserved-moment correction.  Targets of the exact BGK update with
+      // the equilibrium shift (omega tau = 1), deviation form, xi units,
+      // g_xi = g / r: mass and Jx unchanged, Jy - rho g_xi,
+      // Exi - 2 g_xi Jy + rho g_xi^2 (the gravity terms are ~1e-5 of the
+      // sums, float32 is enough for them).
+      const MomentsDF& nw = m;
+      const float gr = a.df_g_r[0];
+      const DF tjy = df_add(dev.Jy, -rf * gr);
+      const DF te = df_add(dev.Exi, fmaf(rf * gr, gr, -2.0f * gr * dev.Jy.hi));
+      // defects (~1e-8 of the sums): one rounding of the difference at most
+      const float dm = (nw.rho.hi - dev.rho.hi) + (nw.rho.lo - dev.rho.lo);
+      const float djx = (nw.Jx.hi - dev.Jx.hi) + (nw.Jx.lo - dev.Jx.lo);
+      const float djy = (nw.Jy.hi - tjy.hi) + (nw.Jy.lo - tjy.lo);
+      const float de = (nw.Exi.hi - te.hi) + (nw.Exi.lo - te.lo);
+      d[0] += de - dm;
+      d[1] += (-0.5f * de - djx) * 0.5f;  // xi = (1, 0)
+      d[2] += (-0.5f * de + djx) * 0.5f;  // xi = (-1, 0)
+      d[3] += (-0.5f * de - djy) * 0.5f;  // xi = (0, 1)
+      d[4] += (-0.5f * de + djy) * 0.5f;  // xi = (0, -1)
+    }
   }
-  // conserved-moment correction.  Targets of the exact BGK update with the
-  // equilibrium shift (omega tau = 1), deviation form, xi units, g_xi = g / r:
-  //   mass and Jx unchanged, Jy - rho g_xi, Exi - 2 g_xi Jy + rho g_xi^2
-  // (the gravity terms are ~1e-5 of the sums, float32 is enough for them).
-  const MomentsDF nw = moment_sums_split(d);
-  const float gr = a.df_g_r[0];
-  const DF tjy = df_add(dev.Jy, -rf * gr);
-  const DF te = df_add(dev.Exi, fmaf(rf * gr, gr, -2.0f * gr * dev.Jy.hi));
-  // defects: the two sums agree to ~1e-8, so hi - hi is exact (Sterbenz)
-  const float dm = (nw.rho.hi - dev.rho.hi) + (nw.rho.lo - dev.rho.lo);
-  const float djx = (nw.Jx.hi - dev.Jx.hi) + (nw.Jx.lo - dev.Jx.lo);
-  const float djy = (nw.Jy.hi - tjy.hi) + (nw.Jy.lo - tjy.lo);
-  const float de = (nw.Exi.hi - te.hi) + (nw.Exi.lo - te.lo);
-  d[0] += de - dm;
-  d[1] += (-0.5f * de - djx) * 0.5f;  // xi = (1, 0)
-  d[2] += (-0.5f * de + djx) * 0.5f;  // xi = (-1, 0)
-  d[3] += (-0.5f * de - djy) * 0.5f;  // xi = (0, 1)
-  d[4] += (-0.5f * de + djy) * 0.5f;  // xi = (0, -1)
 }
 
 // Per-pair constants for rolled loops: representative R_k and shell index.
