@@ -128,12 +128,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def rt_lattice(lx, ly, precision, rho0=None):
+def rt_lattice(lx, ly, precision, rho0=None, **kw):
     import synth
     from paper_1703_00186_gb300.lbm import Lattice
     rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 32, 0)
     r0 = float(rho.mean()) if rho0 is None else rho0
-    lat = Lattice(lx, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb, precision=precision, rho0=r0)
+    lat = Lattice(lx, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb, precision=precision, rho0=r0, **kw)
     lat.init(rho, ux, uy, T)
     return lat, (rho, ux, uy, T)
 
@@ -453,7 +453,16 @@ def main():
         barrier(torch, world)
         t_ms = dist_max(time_steps(lat, K, torch), torch, world)
         out["fp32"] = {"ms": t_ms, "mlups": world * sites * K / (t_ms * 1e-3) / 1e6,
-                       "finite": lat.check_finite()}
+                       "finite": lat.check_finite(), "loads": lat.step_path()}
+        del lat
+        torch.cuda.empty_cache()
+        # the same step with its pull sources staged in shared memory by TMA
+        lat, _ = rt_lattice(lx, ly, "fp32", tma_loads=True)
+        lat.step(W)
+        barrier(torch, world)
+        t_tma = dist_max(time_steps(lat, K, torch), torch, world)
+        out["fp32"]["mlups_tma_loads"] = world * sites * K / (t_tma * 1e-3) / 1e6
+        out["fp32"]["tma_path"] = lat.step_path()
         del lat
         torch.cuda.empty_cache()
     if "fp64df" in only:
@@ -598,6 +607,8 @@ def main():
                              "hbm_gbs": BYTES_PER_SITE_FP32 * sites / t_launch / 1e9,
                              "hbm_frac_of_measured": BYTES_PER_SITE_FP32 * sites / t_launch / 1e9 / HBM_GBS_MEASURED,
                              "hbm_peak_source": HBM_PEAK_SOURCE,
+                             "loads": f32["loads"], "mlups_tma_loads": f32["mlups_tma_loads"],
+                             "tma_path": f32["tma_path"],
                              "finite_after_timed_steps": f32["finite"]}
     if "fp64df" in out:
         d = out["fp64df"]

@@ -91,7 +91,14 @@ enum {
    * the "projection onto a basis of Hermite polynomials" of Sect. 2.  Mass,
    * momentum and energy change exactly as in plain BGK.  The adjoint calls
    * refuse contexts with this flag. */
-  LBM_FLAG_REGULARIZED = 2
+  LBM_FLAG_REGULARIZED = 2,
+  /* LBM_FP32_SHIFTED steps stage each tile's pull sources in shared memory
+   * with TMA loads instead of per-thread loads, where lx is a multiple of 4,
+   * y has walls and the buffers are 16-byte aligned (otherwise the flag is
+   * ignored).  Bit-identical results.  Measured slower than the default on
+   * GB300 (the per-tile block barrier costs more issue slots than the load
+   * latency it hides); kept for comparison. */
+  LBM_FLAG_TMA_LOADS = 4
 };
 
 typedef struct lbm_params {
@@ -147,6 +154,13 @@ int lbm_step_from(lbm_ctx* ctx, const void* src, void* dst);
 
 /* Device pointer of the buffer holding the current state. */
 void* lbm_current(const lbm_ctx* ctx);
+
+/* Which kernel lbm_step runs for this context: LBM_PATH_TMA when the
+ * LBM_FP32_SHIFTED step stages its pull sources with TMA loads (requested
+ * with LBM_FLAG_TMA_LOADS and supported), LBM_PATH_PLAIN otherwise
+ * (per-thread loads).  LBM_ERR_INVALID for a NULL context. */
+enum { LBM_PATH_PLAIN = 0, LBM_PATH_TMA = 1 };
+int lbm_step_path(const lbm_ctx* ctx);
 
 /* Macroscopic fields of eq. (2) of the state f (NULL = current state), as
  * raw moments of the stored populations: rho, u = j / rho,

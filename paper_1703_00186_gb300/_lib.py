@@ -24,6 +24,9 @@ LBM_FP32_SHIFTED = 1
 LBM_FP64_DF = 2
 LBM_FLAG_PERIODIC_Y = 1
 LBM_FLAG_REGULARIZED = 2
+LBM_FLAG_TMA_LOADS = 4
+LBM_PATH_PLAIN = 0
+LBM_PATH_TMA = 1
 LBM_NOALLOC_MAX_LX = 16384
 LBM_NOBS = 8
 
@@ -58,6 +61,7 @@ SIGNATURES = {
     "lbm_step": (c_int, [c_void_p, c_int]),
     "lbm_step_from": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_current": (c_void_p, [c_void_p]),
+    "lbm_step_path": (c_int, [c_void_p]),
     "lbm_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_profiles": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_step_observe": (c_int, [c_void_p, c_int, c_int, c_void_p, P(c_int)]),

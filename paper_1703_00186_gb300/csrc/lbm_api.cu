@@ -22,6 +22,7 @@ cudaError_t launch_finite(int prec, const void* src, const LatticeArgs& a, unsig
                           cudaStream_t s);
 cudaError_t launch_profiles(int prec, const void* src, double* out, const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_step_observe(const void* src, void* dst, const LatticeArgs& a, double* obs, cudaStream_t s);
+bool step_uses_tma(const LatticeArgs& a, const void* src);
 cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, double* lam_out,
                            const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux,
@@ -67,7 +68,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     std::snprintf(err, errlen, "invalid physical parameters (need tau > 0.5, finite g, T_wall > 0)");
     return LBM_ERR_INVALID;
   }
-  if (p.flags & ~(LBM_FLAG_PERIODIC_Y | LBM_FLAG_REGULARIZED)) {
+  if (p.flags & ~(LBM_FLAG_PERIODIC_Y | LBM_FLAG_REGULARIZED | LBM_FLAG_TMA_LOADS)) {
     std::snprintf(err, errlen, "unknown flags 0x%x", p.flags);
     return LBM_ERR_INVALID;
   }
@@ -90,6 +91,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   }
   a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;
   a->regularized = (p.flags & LBM_FLAG_REGULARIZED) ? 1 : 0;
+  a->tma_loads = (p.flags & LBM_FLAG_TMA_LOADS) ? 1 : 0;
   a->tau = p.tau;
   a->g = p.g;
   a->omega = 1.0 / p.tau;
@@ -275,6 +277,13 @@ int lbm_step_from(lbm_ctx* c, const void* src, void* dst) {
 }
 
 void* lbm_current(const lbm_ctx* c) { return c ? c->buf[c->cur] : nullptr; }
+
+int lbm_step_path(const lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID;
+  if (c->p.precision != LBM_FP32_SHIFTED) return LBM_PATH_PLAIN;
+  return step_uses_tma(c->args, c->buf[c->cur]) && step_uses_tma(c->args, c->buf[1 - c->cur]) ? LBM_PATH_TMA
+                                                                                               : LBM_PATH_PLAIN;
+}
 
 int lbm_moments(lbm_ctx* c, const void* f, double* rho, double* ux, double* uy, double* T) {
   if (!c) return LBM_ERR_INVALID;

@@ -110,6 +110,7 @@ struct LatticeArgs {
   // (idx32 != 0): the pull source of population l of an interior column is
   // site + pull_off[l], its destination site + plane_off[l].
   int idx32;
+  int tma_loads;         // LBM_FLAG_TMA_LOADS
   int pull_off[NPOP];    // l plane - xi_ly lx - xi_lx
   int plane_off[NPOP];   // l plane
 };

@@ -48,7 +48,8 @@ class Lattice:
 
     def __init__(self, lx: int, ly: int, tau: float, g: float = 0.0, t_top: float = 1.0,
                  t_bottom: float = 1.0, precision: str = "fp64", rho0: float = 1.0,
-                 periodic_y: bool = False, regularized: bool = False, device=None, stream=None):
+                 periodic_y: bool = False, regularized: bool = False, tma_loads: bool = False,
+                 device=None, stream=None):
         self.lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -57,7 +58,8 @@ class Lattice:
         self.precision = precision
         prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED, "fp64df": L.LBM_FP64_DF}[precision]
         self.dtype = torch.float32 if prec == L.LBM_FP32_SHIFTED else torch.float64
-        flags = (L.LBM_FLAG_PERIODIC_Y if periodic_y else 0) | (L.LBM_FLAG_REGULARIZED if regularized else 0)
+        flags = ((L.LBM_FLAG_PERIODIC_Y if periodic_y else 0) | (L.LBM_FLAG_REGULARIZED if regularized else 0)
+                 | (L.LBM_FLAG_TMA_LOADS if tma_loads else 0))
         self.params = L.LbmParams(self.lx, self.ly, prec, flags,
                                   float(tau), float(g), float(t_top), float(t_bottom), float(rho0))
         self.tau, self.g, self.t_top, self.t_bottom, self.rho0 = tau, g, t_top, t_bottom, rho0
@@ -186,6 +188,13 @@ class Lattice:
 
     def status(self) -> int:
         return self.lib.lbm_status(self.ctx)
+
+    def step_path(self) -> str:
+        """'tma' when step() stages the pull sources with TMA loads, else 'plain'."""
+        rc = self.lib.lbm_step_path(self.ctx)
+        if rc < 0:
+            raise L.LBMError(rc, "lbm_step_path")
+        return "tma" if rc == L.LBM_PATH_TMA else "plain"
 
     def constants(self):
         r = ctypes.c_double()

@@ -371,3 +371,29 @@ def test_step_from_equals_step():
     lat.step_from(src, dst)
     lat.step(1)
     np.testing.assert_array_equal(dst[:, 3:-3].cpu().numpy(), lat.state()[:, 3:-3].cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# FP32 shifted storage: the TMA-staged step against the plain-load step.
+
+@pytest.mark.parametrize("lx,ly", [(64, 40), (100, 37), (36, 6), (8, 9), (2048, 64)])
+def test_fp32_tma_staged_step_is_bit_identical_to_plain_loads(lx, ly):
+    # ragged tiles in x (100, 36, 8) and y (37, 9), seam columns read with
+    # plain loads, wall rows, and a row of many tiles
+    rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 2, 5, delta=0.4)
+    kw = dict(tau=0.7, g=1e-4, t_top=tt, t_bottom=tb, precision="fp32", rho0=float(rho.mean()))
+    a = Lattice(lx, ly, tma_loads=True, **kw).init(rho, ux, uy, T)
+    b = Lattice(lx, ly, **kw).init(rho, ux, uy, T)
+    assert a.step_path() == "tma" and b.step_path() == "plain"
+    a.step(7)
+    b.step(7)
+    assert a.status() == 0 and b.status() == 0
+    assert torch.equal(a.state()[:, 3:-3], b.state()[:, 3:-3])
+
+
+def test_fp32_step_path_falls_back_to_plain_loads():
+    kw = dict(tau=0.7, precision="fp32", tma_loads=True)
+    assert Lattice(66, 12, **kw).step_path() == "plain"                    # lx not a multiple of 4
+    assert Lattice(64, 12, periodic_y=True, **kw).step_path() == "plain"   # y wraps
+    assert Lattice(64, 12, tau=0.7, tma_loads=True).step_path() == "plain"  # float64 modes
+    assert Lattice(64, 12, tau=0.7, precision="fp32").step_path() == "plain"  # not requested
