@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restri
     for (int l = 0; l < NPOP; ++l) f[l] = dec(l, g[l]);
   }
   walls(src, x, y, a, f, dec, [](int, double v) { return v; });
-  const Moments mo = moment_sums([&](int l) { return f[l]; });
+  const Moments mo = site_moments([&](int l) { return f[l]; });
   const SiteFields sf = site_fields(mo, a);
   const double theta = sf.T + a.tshift;
   const double uys = sf.uy - a.tau_g_xi;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(ABX * ABY) moments_vjp_kernel(const void* __re
   if (x >= a.lx || y >= a.ly) return;
   const S* src = static_cast<const S*>(f_);
   Dec<PREC> dec{&a};
-  const Moments mo = moment_sums([&](int l) { return dec(l, src[sidx(a, l, y, x)]); });
+  const Moments mo = site_moments([&](int l) { return dec(l, src[sidx(a, l, y, x)]); });
   const SiteFields sf = site_fields(mo, a);
   const long long i = (long long)y * a.lx + x;
   const double gr = g_rho ? g_rho[i] : 0.0;

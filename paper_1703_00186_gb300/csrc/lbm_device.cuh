@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "dfloat.cuh"
+#include "fixed96.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -182,6 +183,42 @@ __device__ __forceinline__ Moments moment_sums(Get get) {
   return mo;
 }
 
+// The same four sums formed exactly in 96-bit fixed point on the integer
+// pipe and rounded once to float64 (fixed96.cuh): the correctly rounded exact
+// sums.  Returns false, leaving `mo` unset, when a population lies outside
+// the fixed-point range (|f| >= 4, infinities, NaN).
+template <typename Get>
+__device__ __forceinline__ bool moment_sums_exact(Get get, Moments& mo) {
+  bool ok = true;
+  Fix96 r = to_fix(get(0), ok);
+  Fix96 jx{0u, 0u, 0u}, jy{0u, 0u, 0u}, e{0u, 0u, 0u};
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const Fix96 p = to_fix(get(2 * k + 1), ok), m = to_fix(get(2 * k + 2), ok);
+    const Fix96 s = fix_add(p, m), d = fix_sub(p, m);
+    r = fix_add(r, s);
+    e = fix_axpy(e, s, rep_x(k) * rep_x(k) + rep_y(k) * rep_y(k));
+    jx = fix_axpy(jx, d, rep_x(k));
+    jy = fix_axpy(jy, d, rep_y(k));
+  }
+  if (!ok) return false;
+  mo.rho = fix_to_double(r);
+  mo.Jx = fix_to_double(jx);
+  mo.Jy = fix_to_double(jy);
+  mo.Exi = fix_to_double(e);
+  return true;
+}
+
+// Moment sums of 37 float64 values: exact (moment_sums_exact) where the
+// populations fit the fixed-point range, float64 additions (moment_sums)
+// otherwise, so that infinities and NaNs still propagate.
+template <typename Get>
+__device__ __forceinline__ Moments site_moments(Get get) {
+  Moments mo;
+  if (!moment_sums_exact(get, mo)) mo = moment_sums(get);
+  return mo;
+}
+
 // Double-float accumulation (Knuth's TwoSum and the FMA exact product): a
 // sum is kept as hi + lo, where every addition into hi is error-free and the
 // rounding errors are collected in lo.  For sums of float32 values with small
@@ -346,7 +383,7 @@ __device__ __forceinline__ SiteFields site_fields(const Moments& m, const Lattic
 // BGK collide in float64 (eq. 1) with the gravity equilibrium shift.  Returns
 // the pre-collide site fields (rho, u in xi units, T).
 __device__ __forceinline__ SiteFields collide_fp64(double (&f)[NPOP], const LatticeArgs& a) {
-  const Moments mo = moment_sums([&](int l) { return f[l]; });
+  const Moments mo = site_moments([&](int l) { return f[l]; });
   const SiteFields sf = site_fields(mo, a);
   const double theta = sf.T + a.tshift;
   const double uys = sf.uy - a.tau_g_xi;
@@ -507,7 +544,7 @@ __host__ __device__ constexpr int shell_first_pair(int j) {
 template <int NT>
 __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const LatticeArgs& a, double (*s_f)[NT],
                                                 int tid, double* __restrict__ dst, int x, int y) {
-  const Moments mo = moment_sums([&](int l) { return f[l]; });
+  const Moments mo = site_moments([&](int l) { return f[l]; });
   const SiteFields sf = site_fields(mo, a);
 #pragma unroll
   for (int l = 1; l < NPOP; ++l) s_f[l][tid] = f[l];

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128) noalloc_adjoint_kernel(const void* __rest
     for (int l = 0; l < NPOP; ++l) f[l] = dec(l, g[l]);
   }
   walls(src, x, y, a, f, dec, [](int, double v) { return v; });
-  const Moments mo = moment_sums([&](int l) { return f[l]; });
+  const Moments mo = site_moments([&](int l) { return f[l]; });
   const SiteFields sf = site_fields(mo, a);
   const double theta = sf.T + a.tshift;
   const double uys = sf.uy - a.tau_g_xi;

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(BX * BY) moments_kernel(const void* __restrict
   if (x >= a.lx || y >= a.ly) return;
   const S* src = static_cast<const S*>(src_);
   Codec<PREC> codec{&a};
-  Moments mo = moment_sums([&](int l) { return codec(l, src[sidx(a, l, y, x)]); });
+  Moments mo = site_moments([&](int l) { return codec(l, src[sidx(a, l, y, x)]); });
   const SiteFields sf = site_fields(mo, a);
   const long long i = (long long)y * a.lx + x;
   if (rho) rho[i] = sf.rho;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) profiles_kernel(const void* __restrict__ 
 #pragma unroll
   for (int i = 0; i < NOBS; ++i) acc[i] = 0.0;
   for (int x = threadIdx.x; x < a.lx; x += blockDim.x) {
-    const Moments mo = moment_sums([&](int l) { return codec(l, src[sidx(a, l, y, x)]); });
+    const Moments mo = site_moments([&](int l) { return codec(l, src[sidx(a, l, y, x)]); });
     const SiteFields sf = site_fields(mo, a);
     double o[NOBS];
     site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy + 0.5 * a.g, sf.T, o);

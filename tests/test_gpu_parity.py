@@ -122,6 +122,36 @@ def test_rayleigh_taylor_64x128_100_steps_fp64():
         assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max() + 1e-15
 
 
+def test_moment_sums_are_the_correctly_rounded_exact_sums():
+    # The float64 moment sums are formed exactly (fixed point on the integer
+    # pipe) and rounded once: rho must equal the exact rational sum of the
+    # stored populations rounded to nearest, bit for bit, for populations of
+    # mixed signs and magnitudes (all >= 2^-30, so nothing is truncated), and
+    # for a site holding a population outside the fixed-point range (|f| >= 4,
+    # float64 fallback) it must still be within float64 rounding.
+    from fractions import Fraction
+    lx, ly = 19, 7
+    rng = np.random.default_rng(93)
+    f = noisy_state(lx, ly, 92, eps=0.05)
+    phys = f[:, 3:-3]
+    phys *= np.where(rng.random(phys.shape) < 0.1, -1.0, 1.0)          # some negative populations
+    phys *= 2.0 ** rng.integers(-20, 3, phys.shape)                       # spread of exponents
+    small = (np.abs(phys) < 2.0 ** -30) & (phys != 0)
+    phys[small] = np.copysign(2.0 ** -30, phys[small])
+    phys[rng.random(phys.shape) < 0.02] = 0.0
+    phys[:, 2, 5] = 3.999999                                              # top of the exact range
+    phys[7, 4, 11] = 5.0                                                  # outside: float64 fallback
+    lat = make(M.Params(lx, ly, tau=0.8))
+    rho = lat.moments(to_dev(f))[0].cpu().numpy()
+    for y in range(ly):
+        for x in range(lx):
+            exact = sum(Fraction(float(v)) for v in phys[:, y, x])
+            if (y, x) == (4, 11):
+                assert abs(rho[y, x] - float(exact)) <= 1e-14 * np.abs(phys[:, y, x]).sum()
+            else:
+                assert rho[y, x] == float(exact), (y, x)
+
+
 def test_moments_match_eq2():
     lx, ly = 33, 20
     f = noisy_state(lx, ly, 9)
