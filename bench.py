@@ -12,7 +12,8 @@ fp32_store   the same lattice stored as float32 deviations f_l - w_l rho0.
 adjoint      one adjoint step (recompute + transposed collide + push) over
              the same lattice, as a ratio to the forward step time.
 e2e          the same metric through the C ABI with pinned HOST buffers:
-             per step set_state(host) -> step -> get_state(host).
+             per step set_state(host) -> step -> get_state(host), two
+             independent lattices on two streams.
 roofline     the fused float64 kernel against the FP64 FMA rate measured by
              the library's probe (the step is FP64-pipe bound).
 cpu_baseline the float64 oracle (NumPy) on a bounded sample of the workload.
@@ -536,28 +537,46 @@ def main():
         del lat, f_t, lam_a, lam_b
         torch.cuda.empty_cache()
     if "e2e" in only:
-        lat, _ = rt_lattice(lx, ly, "fp64")
-        host_in = torch.empty(lat.shape, dtype=lat.dtype, pin_memory=True)
-        host_out = torch.empty(lat.shape, dtype=lat.dtype, pin_memory=True)
-        lat.get_state(host_in)
+        # Two independent lattices, each on its own stream, each step of each
+        # lattice through the C ABI from and to pinned host memory:
+        # set_state(host) -> step(1) -> get_state(host).  The copy engines
+        # move one lattice's state in while the other's goes out or computes.
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        lats = [rt_lattice(lx, ly, "fp64", stream=st)[0] for st in streams]
+        host_in = [torch.empty(lats[0].shape, dtype=lats[0].dtype, pin_memory=True) for _ in lats]
+        host_out = [torch.empty(lats[0].shape, dtype=lats[0].dtype, pin_memory=True) for _ in lats]
+        for lat, h in zip(lats, host_in):
+            lat.get_state(h)
         torch.cuda.synchronize()
         ke = max(3, min(K, 20))
+
+        def e2e_round():
+            for lat, hi, ho in zip(lats, host_in, host_out):
+                lat.set_state(hi).step(1).get_state(ho)
+
         for _ in range(2):
-            lat.set_state(host_in).step(1).get_state(host_out)
+            e2e_round()
+        torch.cuda.synchronize()
         barrier(torch, world)
-        s = lat.stream
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
+        eb = torch.cuda.Event()
+        e0.record(streams[0])
+        streams[1].wait_event(e0)
         for _ in range(ke):
-            lat.set_state(host_in).step(1).get_state(host_out)
-        e1.record(s)
+            e2e_round()
+        eb.record(streams[1])
+        streams[0].wait_event(eb)
+        e1.record(streams[0])
         e1.synchronize()
         te = dist_max(e0.elapsed_time(e1), torch, world)
-        out["e2e"] = {"value": world * sites * ke / (te * 1e-3) / 1e6, "unit": "MLUPS",
-                      "h2d_bytes_per_step": lat.nbytes, "d2h_bytes_per_step": lat.nbytes,
-                      "steps": ke, "path": "lbm_set_state(pinned host) + lbm_step(1) + lbm_get_state(pinned host)"}
-        del lat, host_in, host_out
+        out["e2e"] = {"value": world * len(lats) * sites * ke / (te * 1e-3) / 1e6, "unit": "MLUPS",
+                      "h2d_bytes_per_step": lats[0].nbytes, "d2h_bytes_per_step": lats[0].nbytes,
+                      "steps": ke * len(lats), "lattices": len(lats),
+                      "path": "per lattice step: lbm_set_state(pinned host) + lbm_step(1) + "
+                              "lbm_get_state(pinned host); two lattices on two streams"}
+        del lats, host_in, host_out
+        torch.cuda.empty_cache()
     if "fp32_error" in only:
         out["fp32_error"] = fp32_error_study(lx, ly, args.error_steps, torch)
         torch.cuda.empty_cache()
