@@ -6,8 +6,9 @@
 // product by FMA) and the double-word algorithms analysed by Joldes, Muller
 // and Popescu, "Tight and rigorous error bounds for basic building blocks of
 // double-word arithmetic", ACM TOMS 44 (2017):
-//   DWPlusFP, AccurateDWPlusDW, DWTimesFP (FMA variant), DWTimesDW (FMA
-//   variant), each with a relative error of a few u^2, u = 2^-24.
+//   DWPlusFP, AccurateDWPlusDW, SloppyDWPlusDW, DWTimesFP (FMA variant),
+//   DWTimesDW (FMA variant), each with a relative error of a few u^2,
+//   u = 2^-24 (SloppyDWPlusDW: relative to |x| + |y|).
 // On GB300 the FP32 pipe issues 64 times the FP64 rate, so a handful of
 // float32 operations per emulated operation is still far cheaper.
 #pragma once
@@ -43,6 +44,15 @@ __device__ __forceinline__ DF df_from(float a) { return {a, 0.f}; }
 __device__ __forceinline__ DF df_add(DF x, float y) {
   const DF s = df_two_sum(x.hi, y);
   return df_fast_two_sum(s.hi, x.lo + s.lo);
+}
+
+// SloppyDWPlusDW (same paper): x + y for double-words in 11 operations.  Its
+// error is a few u^2 relative to |x| + |y| (not to |x + y|), so it is used
+// only where the sum does not cancel: adding a smaller correction to a
+// dominant term of the equilibrium polynomial.
+__device__ __forceinline__ DF df_add_fast(DF x, DF y) {
+  const DF s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
 }
 
 // AccurateDWPlusDW: x + y for double-words.
