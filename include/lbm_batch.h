@@ -13,8 +13,9 @@
  *
  * OWNERSHIP.  The caller owns every lattice buffer (two per lattice, in the
  * state layout of include/lbm.h) and the stream.  The batch allocates its
- * own small device tables (lattice parameters and tile offsets) and its CUDA
- * graphs; lbm_batch_destroy releases them.
+ * own device tables (lattice parameters, tile offsets, and for every tile
+ * shape the lattice of each tile: 4 bytes per tile, about 1 MB per shape for
+ * 33 M sites) and its CUDA graphs; lbm_batch_destroy releases them.
  *
  * ERRORS.  As in include/lbm.h: LBM_OK or a negative LBM_ERR_* code, with a
  * message from lbm_batch_last_error().

@@ -1,7 +1,7 @@
 // Batched stepping of many independent D2Q37 lattices (include/lbm_batch.h).
 //
-// One launch advances every lattice of the batch by one step: block b finds
-// its lattice by a binary search of the tile offsets, copies that lattice's
+// One launch advances every lattice of the batch by one step: block b reads
+// its lattice from a per-tile table (one load), copies that lattice's
 // constants into shared memory and runs the fused propagate + bc + collide
 // on its tile (the same device code as the single-lattice kernel).  n steps
 // are captured into a CUDA graph on a private stream and replayed on the
@@ -62,14 +62,10 @@ struct BCodec<LBM_FP32_SHIFTED> {
 // calls it (threads outside the lattice skip the work but reach the barriers).
 template <int PREC, int TBX, int TBY, bool DFARITH, bool COHERENT>
 __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, const long long* __restrict__ tile_start,
-                                           int n, int parity, long long b, LatticeArgs& sa, const void*& s_src,
-                                           void*& s_dst) {
+                                           const int* __restrict__ tile_lattice, int parity, long long b,
+                                           LatticeArgs& sa, const void*& s_src, void*& s_dst) {
   using T = typename BCodec<PREC>::T;
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(tile_start + mid) <= b) lo = mid; else hi = mid - 1;
-  }
+  const int lo = __ldg(tile_lattice + b);  // the lattice that owns tile b
   const int tid = threadIdx.y * TBX + threadIdx.x;
   {
     static_assert(sizeof(LatticeArgs) % 8 == 0, "LatticeArgs must be a multiple of 8 bytes");
@@ -116,11 +112,11 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
 template <int PREC, int TBX, int TBY, bool DFARITH = false>
 __global__ void __launch_bounds__(TBX * TBY, PREC == LBM_FP32_SHIFTED ? 5 * 128 / (TBX * TBY) : 0) batch_step_kernel(const BatchEntry* __restrict__ ent,
                                                                const long long* __restrict__ tile_start,
-                                                               int n, int parity) {
+                                                               const int* __restrict__ tile_lattice, int parity) {
   __shared__ __align__(16) LatticeArgs sa;
   __shared__ const void* s_src;
   __shared__ void* s_dst;
-  batch_tile<PREC, TBX, TBY, DFARITH, false>(ent, tile_start, n, parity, blockIdx.x, sa, s_src, s_dst);
+  batch_tile<PREC, TBX, TBY, DFARITH, false>(ent, tile_start, tile_lattice, parity, blockIdx.x, sa, s_src, s_dst);
 }
 
 // Grid barrier of the persistent kernel with a bounded wait.  State in global
@@ -182,7 +178,8 @@ __device__ bool grid_barrier(GridBarrier* bar, unsigned int expected, unsigned l
 // populations other blocks have just written (coherent loads).
 template <int PREC, bool DFARITH>
 __global__ void __launch_bounds__(128, PREC == LBM_FP32_SHIFTED ? 5 : 0) batch_persistent_kernel(const BatchEntry* __restrict__ ent,
-                                                               const long long* __restrict__ tile_start, int n,
+                                                               const long long* __restrict__ tile_start,
+                                                               const int* __restrict__ tile_lattice,
                                                                long long tiles, int parity0, int steps,
                                                                GridBarrier* bar, unsigned long long budget_ns) {
   __shared__ __align__(16) LatticeArgs sa;
@@ -191,7 +188,7 @@ __global__ void __launch_bounds__(128, PREC == LBM_FP32_SHIFTED ? 5 : 0) batch_p
   for (int st = 0; st < steps; ++st) {
     const int parity = (parity0 + st) & 1;
     for (long long b = blockIdx.x; b < tiles; b += gridDim.x)
-      batch_tile<PREC, 32, 4, DFARITH, true>(ent, tile_start, n, parity, b, sa, s_src, s_dst);
+      batch_tile<PREC, 32, 4, DFARITH, true>(ent, tile_start, tile_lattice, parity, b, sa, s_src, s_dst);
     if (st + 1 < steps && !grid_barrier(bar, gridDim.x, budget_ns)) return;
   }
 }
@@ -203,26 +200,26 @@ __global__ void barrier_selftest_kernel(GridBarrier* bar, unsigned long long bud
 }
 
 template <int PREC, int I>
-cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long long* ts, int n, int parity,
+cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long long* ts, const int* tl, int parity,
                           cudaStream_t s) {
   constexpr int BX = kTileBX[I], BY = kTileBY[I];
   if constexpr (PREC == LBM_FP64_DF)
-    batch_step_kernel<LBM_FP64, BX, BY, true><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, n, parity);
+    batch_step_kernel<LBM_FP64, BX, BY, true><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, tl, parity);
   else
-    batch_step_kernel<PREC, BX, BY><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, n, parity);
+    batch_step_kernel<PREC, BX, BY><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, tl, parity);
   return cudaGetLastError();
 }
 
 template <int PREC>
-cudaError_t launch_tile(int tile, long long blocks, const BatchEntry* ent, const long long* ts, int n, int parity,
-                        cudaStream_t s) {
+cudaError_t launch_tile(int tile, long long blocks, const BatchEntry* ent, const long long* ts, const int* tl,
+                        int parity, cudaStream_t s) {
   switch (tile) {
-    case 0: return launch_tile_i<PREC, 0>(blocks, ent, ts, n, parity, s);
-    case 1: return launch_tile_i<PREC, 1>(blocks, ent, ts, n, parity, s);
-    case 2: return launch_tile_i<PREC, 2>(blocks, ent, ts, n, parity, s);
-    case 3: return launch_tile_i<PREC, 3>(blocks, ent, ts, n, parity, s);
-    case 4: return launch_tile_i<PREC, 4>(blocks, ent, ts, n, parity, s);
-    default: return launch_tile_i<PREC, 5>(blocks, ent, ts, n, parity, s);
+    case 0: return launch_tile_i<PREC, 0>(blocks, ent, ts, tl, parity, s);
+    case 1: return launch_tile_i<PREC, 1>(blocks, ent, ts, tl, parity, s);
+    case 2: return launch_tile_i<PREC, 2>(blocks, ent, ts, tl, parity, s);
+    case 3: return launch_tile_i<PREC, 3>(blocks, ent, ts, tl, parity, s);
+    case 4: return launch_tile_i<PREC, 4>(blocks, ent, ts, tl, parity, s);
+    default: return launch_tile_i<PREC, 5>(blocks, ent, ts, tl, parity, s);
   }
 }
 
@@ -240,6 +237,7 @@ struct lbm_batch {
   std::vector<void*> fa, fb;
   BatchEntry* d_ent;
   long long* d_tiles[kTiles];  // tile offsets per shape
+  int* d_tile_lat[kTiles];     // per shape: the lattice of every tile
   long long blocks[kTiles];
   int tile;
   int parity;
@@ -269,17 +267,19 @@ int bcuda(lbm_batch* b, cudaError_t e, const char* what) {
 cudaError_t launch_batch(const lbm_batch* b, int parity, cudaStream_t s) {
   const int t = b->tile;
   if (b->precision == LBM_FP64_DF)
-    return launch_tile<LBM_FP64_DF>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
+    return launch_tile<LBM_FP64_DF>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->d_tile_lat[t], parity, s);
   if (b->precision == LBM_FP64)
-    return launch_tile<LBM_FP64>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
-  return launch_tile<LBM_FP32_SHIFTED>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->n, parity, s);
+    return launch_tile<LBM_FP64>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->d_tile_lat[t], parity, s);
+  return launch_tile<LBM_FP32_SHIFTED>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->d_tile_lat[t], parity, s);
 }
 
 void free_batch(lbm_batch* b) {
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
-  for (int t = 0; t < kTiles; ++t)
+  for (int t = 0; t < kTiles; ++t) {
     if (b->d_tiles[t]) cudaFree(b->d_tiles[t]);
+    if (b->d_tile_lat[t]) cudaFree(b->d_tile_lat[t]);
+  }
   if (b->d_ent) cudaFree(b->d_ent);
   if (b->d_bar) cudaFree(b->d_bar);
   if (b->capture) cudaStreamDestroy(b->capture);
@@ -380,6 +380,16 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
     b->blocks[t] = ts[n];
     if (ts[n] >= (1LL << 31) || cudaMalloc(&b->d_tiles[t], sizeof(long long) * (n + 1)) != cudaSuccess ||
         cudaMemcpy(b->d_tiles[t], ts.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return LBM_ERR_CUDA;
+    }
+    std::vector<int> owner((size_t)ts[n]);
+    for (int i = 0; i < n; ++i)
+      for (long long k = ts[i]; k < ts[i + 1]; ++k) owner[(size_t)k] = i;
+    if (cudaMalloc(&b->d_tile_lat[t], sizeof(int) * owner.size()) != cudaSuccess ||
+        cudaMemcpy(b->d_tile_lat[t], owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
       cudaGetLastError();
       free_batch(b);
       return LBM_ERR_CUDA;
@@ -522,9 +532,10 @@ int launch_persistent(lbm_batch* b, int n, unsigned long long budget_ns) {
   if (rc) return rc;
   const BatchEntry* ent = b->d_ent;
   const long long* ts = b->d_tiles[0];
-  int nl = b->n, parity = b->parity, steps = n;
+  const int* tl = b->d_tile_lat[0];
+  int parity = b->parity, steps = n;
   GridBarrier* bar = b->d_bar;
-  void* args[] = {(void*)&ent, (void*)&ts, (void*)&nl, (void*)&tiles, (void*)&parity, (void*)&steps, (void*)&bar,
+  void* args[] = {(void*)&ent, (void*)&ts, (void*)&tl, (void*)&tiles, (void*)&parity, (void*)&steps, (void*)&bar,
                   (void*)&budget_ns};
   return bcuda(b, cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(32, 4), args, 0, b->stream),
                "persistent step");
