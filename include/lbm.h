@@ -74,8 +74,15 @@ enum {
 };
 
 /* Storage and arithmetic of the step:
- *   LBM_FP64         float64 populations, float64 arithmetic;
- *   LBM_FP32_SHIFTED float32 deviations f_l - w_l rho0 (see collide notes);
+ *   LBM_FP64         float64 populations, float64 arithmetic; the moment sums
+ *                    of eq. (2) are formed exactly (96-bit fixed point on the
+ *                    integer pipe) and rounded once, which is at least as
+ *                    accurate as float64 additions;
+ *   LBM_FP32_SHIFTED float32 deviations f_l - w_l rho0; moment sums with an
+ *                    error of at most 2^-35 per term, double-float density
+ *                    and temperature terms, float32 polynomial, and a
+ *                    correction that makes the collide conserve mass and
+ *                    energy and add exactly rho g to the momentum;
  *   LBM_FP64_DF      float64 populations; the collide runs in double-float
  *                    arithmetic (two float32 words, about 48 significant
  *                    bits) on the FP32 pipe, whose issue rate on GB300 is 64
