@@ -61,6 +61,7 @@ def test_state_bytes_and_argument_checks_need_no_gpu(lib):
                           12345, None) == L.LBM_ERR_SIZE
     assert not ctx.value
     assert lib.lbm_step(None, 1) == L.LBM_ERR_INVALID
+    assert lib.lbm_step_path(None) == L.LBM_ERR_INVALID
 
 
 def test_regularized_flag_only_with_fp64(lib):
