@@ -42,10 +42,9 @@ struct Codec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, bool OBS = false>
+template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ src_,
-                                                       void* __restrict__ dst_, LatticeArgs a,
-                                                       double* __restrict__ obs = nullptr) {
+                                                       void* __restrict__ dst_, LatticeArgs a) {
   using T = typename Codec<PREC>::T;
   const int x = blockIdx.x * BX + threadIdx.x;
   const int y = blockIdx.y * BY + threadIdx.y;
@@ -67,24 +66,6 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
   if (COLLIDE) {
     if constexpr (PREC == LBM_FP64 && REG) {
       collide_fp64_reg(f, a);
-    } else if constexpr (PREC == LBM_FP64 && OBS) {
-      // measurement epilogue: the collide leaves rho and T unchanged and adds
-      // the impulse g_vec to u, so the new state's mid-step velocity is the
-      // pre-collide u + g_vec / 2; warp sums (one row segment) go to the row
-      // totals with one atomic add per quantity.
-      const SiteFields sf = collide_fp64(f, a);
-      double o[NOBS];
-      site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy - 0.5 * a.g, sf.T, o);
-      const unsigned mask = __activemask();
-#pragma unroll
-      for (int i = 0; i < NOBS; ++i) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) o[i] += __shfl_down_sync(mask, o[i], off);
-      }
-      if ((threadIdx.x & 31) == __ffs(mask) - 1) {
-#pragma unroll
-        for (int i = 0; i < NOBS; ++i) atomicAdd(obs + (long long)i * a.ly + y, o[i]);
-      }
     } else if constexpr (PREC == LBM_FP64) {
       collide_fp64(f, a);
     } else {
@@ -92,6 +73,63 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
     }
   }
   store_site(dst, x, y, a, f);
+}
+
+// float64 step with a measurement epilogue: the collide leaves rho and T
+// unchanged and adds the impulse g_vec to u, so the new state's mid-step
+// velocity is the pre-collide u + g_vec / 2.  A warp is one 32-site row
+// segment (BX = 32): every lane takes part in the warp sums, lanes beyond the
+// right edge with zeros.  The sums are exact in fixed point on the integer
+// pipe (float64 shuffles and adds only if a value is outside the fixed-point
+// range) and go to the row totals with one atomic add per quantity.
+__global__ void __launch_bounds__(BX * BY) step_observe_kernel(const double* __restrict__ src,
+                                                               double* __restrict__ dst, LatticeArgs a,
+                                                               double* __restrict__ obs) {
+  static_assert(BX == 32, "one warp per row segment");
+  const int x = blockIdx.x * BX + threadIdx.x;
+  const int y = blockIdx.y * BY + threadIdx.y;
+  if (y >= a.ly) return;  // whole warps
+  double o[NOBS];
+#pragma unroll
+  for (int i = 0; i < NOBS; ++i) o[i] = 0.0;
+  if (x < a.lx) {
+    Codec<LBM_FP64> codec{&a};
+    double f[NPOP];
+    if (fast_site(a, x)) pull_fast(src, site_off(a, y, x), a, f);
+    else pull(src, x, y, a, f);
+    walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+    const SiteFields sf = collide_fp64(f, a);
+    store_site(dst, x, y, a, f);
+    site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy - 0.5 * a.g, sf.T, o);
+  }
+  constexpr unsigned kAll = 0xffffffffu;
+  bool ok = true;
+  Fix96 q[NOBS];
+#pragma unroll
+  for (int i = 0; i < NOBS; ++i) q[i] = to_fix(o[i], ok);
+  if (__all_sync(kAll, ok)) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int i = 0; i < NOBS; ++i) {
+        const Fix96 other{__shfl_down_sync(kAll, q[i].w0, off), __shfl_down_sync(kAll, q[i].w1, off),
+                          __shfl_down_sync(kAll, q[i].w2, off)};
+        q[i] = fix_add(q[i], other);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NOBS; ++i) o[i] = fix_to_double(q[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NOBS; ++i) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) o[i] += __shfl_down_sync(kAll, o[i], off);
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int i = 0; i < NOBS; ++i) atomicAdd(obs + (long long)i * a.ly + y, o[i]);
+  }
 }
 
 template <int PREC>
@@ -420,7 +458,8 @@ cudaError_t launch_profiles(int prec, const void* src, double* out, const Lattic
 cudaError_t launch_step_observe(const void* src, void* dst, const LatticeArgs& a, double* obs, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(obs, 0, sizeof(double) * NOBS * (size_t)a.ly, s);
   if (e != cudaSuccess) return e;
-  step_kernel<LBM_FP64, true, false, false, true><<<site_grid(a), dim3(BX, BY), 0, s>>>(src, dst, a, obs);
+  step_observe_kernel<<<site_grid(a), dim3(BX, BY), 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst),
+                                                         a, obs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long n = (long long)NOBS * a.ly;

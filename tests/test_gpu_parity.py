@@ -152,6 +152,28 @@ def test_moment_sums_are_the_correctly_rounded_exact_sums():
                 assert rho[y, x] == float(exact), (y, x)
 
 
+def test_moment_sums_with_tiny_and_zero_populations():
+    # Populations below 2^-30 keep their bits down to 2^-82 only, so a sum with
+    # such terms is within one unit in the last place of the exact sum (the
+    # rounding may fall on either side of a tie); signed zeros and values at the
+    # bottom of the float64 range are handled without a fallback.
+    from fractions import Fraction
+    lx, ly = 8, 6
+    f = noisy_state(lx, ly, 94, eps=0.05)
+    phys = f[:, 3:-3]
+    tiny = [1e-300, -1e-300, 2.0 ** -60, -(2.0 ** -45), 1e-20, 0.0, -0.0, 3e-12]
+    for i, v in enumerate(tiny):
+        phys[5 + i, i % ly, (3 * i) % lx] = v
+    phys[:, 0, 0] = 0.0
+    phys[0, 0, 0] = 2.0 ** -70                                            # a site of tiny mass
+    lat = make(M.Params(lx, ly, tau=0.8))
+    rho = lat.moments(to_dev(f))[0].cpu().numpy()
+    for y in range(ly):
+        for x in range(lx):
+            exact = float(sum(Fraction(float(v)) for v in phys[:, y, x]))
+            assert abs(rho[y, x] - exact) <= np.spacing(abs(exact)), (y, x, rho[y, x], exact)
+
+
 def test_moments_match_eq2():
     lx, ly = 33, 20
     f = noisy_state(lx, ly, 9)
