@@ -511,31 +511,39 @@ def main():
         del lat
         torch.cuda.empty_cache()
     if "adjoint" in only:
-        lat, _ = rt_lattice(lx, ly, "fp64")
-        lat.step(W)
-        f_t = lat.state().clone()
-        lam_a = lat.new_cotangent(0.0).normal_()
-        lam_b = lat.new_cotangent(0.0)
-        ka = max(3, K // 4)
-        for _ in range(2):
-            lat.adjoint_step(f_t, lam_a, lam_b)
-        s = lat.stream
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(s)
-        for i in range(ka):
-            if i % 2 == 0:
+        def adjoint_times(precision):
+            lat, _ = rt_lattice(lx, ly, precision)
+            lat.step(W)
+            f_t = lat.state().clone()
+            lam_a = lat.new_cotangent(0.0).normal_()
+            lam_b = lat.new_cotangent(0.0)
+            ka = max(3, K // 4)
+            for _ in range(2):
                 lat.adjoint_step(f_t, lam_a, lam_b)
-            else:
-                lat.adjoint_step(f_t, lam_b, lam_a)
-        e1.record(s)
-        e1.synchronize()
-        ta = dist_max(e0.elapsed_time(e1) / ka, torch, world)
-        tf_ms = dist_max(time_steps(lat, ka, torch) / ka, torch, world)
+            s = lat.stream
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            for i in range(ka):
+                if i % 2 == 0:
+                    lat.adjoint_step(f_t, lam_a, lam_b)
+                else:
+                    lat.adjoint_step(f_t, lam_b, lam_a)
+            e1.record(s)
+            e1.synchronize()
+            ta = dist_max(e0.elapsed_time(e1) / ka, torch, world)
+            tf_ms = dist_max(time_steps(lat, ka, torch) / ka, torch, world)
+            del lat, f_t, lam_a, lam_b
+            torch.cuda.empty_cache()
+            return ta, tf_ms
+
+        ta, tf_ms = adjoint_times("fp64")
         out["adjoint"] = {"adjoint_ms_per_step": ta, "forward_ms_per_step": tf_ms, "ratio": ta / tf_ms}
-        del lat, f_t, lam_a, lam_b
-        torch.cuda.empty_cache()
+        # the LBM_FP64_DF mode: double-float forward collide and cotangent sums
+        ta_df, tf_df = adjoint_times("fp64df")
+        out["adjoint"]["fp64df"] = {"adjoint_ms_per_step": ta_df, "forward_ms_per_step": tf_df,
+                                    "ratio": ta_df / tf_df, "ratio_vs_fp64_forward": ta_df / tf_ms}
     if "e2e" in only:
         # Two independent lattices, each on its own stream, each step of each
         # lattice through the C ABI from and to pinned host memory:

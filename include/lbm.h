@@ -88,7 +88,10 @@ enum {
  *                    bits) on the FP32 pipe, whose issue rate on GB300 is 64
  *                    times the FP64 rate.  Propagate and bc are identical
  *                    (bit-exact); every other call treats the state as
- *                    LBM_FP64 (the adjoint linearises the float64 step). */
+ *                    LBM_FP64, except that lbm_adjoint_step evaluates the
+ *                    equilibrium's cotangent sums in double-float too (the
+ *                    transposed Jacobian of the float64 step, to about 48
+ *                    bits). */
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_DF = 2 };
 enum {
   LBM_FLAG_PERIODIC_Y = 1,   /* test mode: no walls, y periodic */

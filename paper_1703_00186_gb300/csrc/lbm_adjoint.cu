@@ -44,6 +44,32 @@ __device__ __forceinline__ long long scratch_idx(const LatticeArgs& a, bool top,
   return (long long)(yh + HALO) * a.lx + x;
 }
 
+// P^T: push each cotangent back to its pull source; the cotangents of wall
+// slots (filled by bc with M(x) q_l) reduce into lam_out's halo-row scratch.
+__device__ __forceinline__ void push_cotangents(const double (&mu)[NPOP], int x, int y, const LatticeArgs& a,
+                                                double* __restrict__ lam_out) {
+  const bool bottom = !a.periodic_y && y < 3;
+  const bool top = !a.periodic_y && y >= a.ly - 3;
+  double wall_sum = 0.0;
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) {
+    int ys = y - vy(l);
+    bool known = true;
+    if (a.periodic_y) {
+      ys = ys < 0 ? ys + a.ly : (ys >= a.ly ? ys - a.ly : ys);
+    } else if (ys < 0 || ys >= a.ly) {
+      known = false;
+    }
+    if (known) {
+      lam_out[sidx(a, l, ys, wrap_x(x - vx(l), a.lx))] = mu[l];
+    } else {
+      wall_sum = fma(ys < 0 ? a.q_bot[l] : a.q_top[l], mu[l], wall_sum);
+    }
+  }
+  if (bottom) lam_out[scratch_idx(a, false, y, x)] = wall_sum;
+  if (top) lam_out[scratch_idx(a, true, a.ly - 1 - y, x)] = wall_sum;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restrict__ f_, const double* __restrict__ lam_in,
                                                             double* __restrict__ lam_out, LatticeArgs a) {
@@ -91,27 +117,125 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restri
     mu[2 * k + 1] = fma(a.omc, lam[2 * k + 1], base + lin);
     mu[2 * k + 2] = fma(a.omc, lam[2 * k + 2], base - lin);
   }
-  // P^T: push each cotangent back to its pull source; wall slots reduce.
-  const bool bottom = !a.periodic_y && y < 3;
-  const bool top = !a.periodic_y && y >= a.ly - 3;
-  double wall_sum = 0.0;
+  push_cotangents(mu, x, y, a, lam_out);
+}
+
+// Adjoint step of an LBM_FP64_DF context: the same transposed Jacobian with
+// the cotangent sums of the equilibrium in double-float arithmetic on the
+// FP32 pipe (as the forward collide of that mode), the pair loop rolled over
+// cotangents staged in shared memory; the site fields, the final cotangent
+// combination and the push stay float64.
+//   SP = sum lam w P,  Scu = sum lam w P_cu xi,  SU = sum lam w dP/dU2,
+//   Sth = sum lam w dP/dtheta (see eq_cotangent).
+__global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const double* __restrict__ src,
+                                                               const double* __restrict__ lam_in,
+                                                               double* __restrict__ lam_out, LatticeArgs a) {
+  __shared__ double s_lam[NPOP][ABX * ABY];
+  const int x = blockIdx.x * ABX + threadIdx.x;
+  const int y = blockIdx.y * ABY + threadIdx.y;
+  if (x >= a.lx || y >= a.ly) return;
+  const int tid = threadIdx.y * ABX + threadIdx.x;
+  Dec<LBM_FP64> dec{&a};
+  SiteFields sf;
+  {
+    double f[NPOP];
+    pull(src, x, y, a, f);
+    walls(src, x, y, a, f, dec, [](int, double v) { return v; });
+    sf = site_fields(site_moments([&](int l) { return f[l]; }), a);
+  }
 #pragma unroll
-  for (int l = 0; l < NPOP; ++l) {
-    int ys = y - vy(l);
-    bool known = true;
-    if (a.periodic_y) {
-      ys = ys < 0 ? ys + a.ly : (ys >= a.ly ? ys - a.ly : ys);
-    } else if (ys < 0 || ys >= a.ly) {
-      known = false;
-    }
-    if (known) {
-      lam_out[sidx(a, l, ys, wrap_x(x - vx(l), a.lx))] = mu[l];
-    } else {
-      wall_sum = fma(ys < 0 ? a.q_bot[l] : a.q_top[l], mu[l], wall_sum);
+  for (int l = 0; l < NPOP; ++l) s_lam[l][tid] = __ldg(lam_in + sidx(a, l, y, x));
+  // site terms and equilibrium coefficients (as collide_fp64_df)
+  const DF ux = df_from_double_bits(sf.ux), uy = df_from_double_bits(sf.uy);
+  const DF theta = df_add(df_from_double_bits(sf.T), dfc(a.df_tshift));
+  const DF uys = df_sub(uy, dfc(a.df_taug_r));
+  const DF U2 = df_mul(df_add(df_mul(ux, ux), df_mul(uys, uys)), dfc(a.df_r2));
+  const DF v_x = df_mul(ux, dfc(a.df_r2)), v_y = df_mul(uys, dfc(a.df_r2));
+  const DF th2 = df_mul(theta, theta);
+  const DF B20 = df_add(df_add(df_mul(U2, -0.25f), df_mul(theta, -1.5f)), 0.5f);
+  const DF B21 = df_scale2(theta, 0.25f);
+  const DF B10 = df_add(df_add(df_scale2(U2, -0.5f), df_scale2(theta, -2.0f)), 1.0f);
+  const DF B11 = df_scale2(theta, 0.5f);
+  const DF B00 = df_add(df_add(df_mul(U2, df_add(df_scale2(U2, 0.125f), -0.5f)),
+                               df_mul(theta, df_add(df_add(U2, -1.0f), theta))), 1.0f);
+  const DF B01 = df_mul(theta, df_sub(df_add(df_scale2(U2, -0.25f), 0.5f), theta));
+  const DF B02 = df_scale2(th2, 0.125f);
+  // d/dU2 and d/dtheta of the shell coefficients
+  const DF dU0 = df_add(df_add(df_scale2(U2, 0.25f), theta), -0.5f);                   // dB00/dU2
+  const DF dU1 = df_scale2(theta, -0.25f);                                              // dB01/dU2
+  const DF dT0 = df_add(df_add(df_scale2(theta, 2.0f), U2), -1.0f);                    // dB00/dtheta
+  const DF dT1 = df_add(df_add(df_scale2(theta, -2.0f), df_scale2(U2, -0.25f)), 0.5f);  // dB01/dtheta
+  const DF dT2 = df_scale2(theta, 0.25f);                                               // dB02/dtheta
+  DF SP, Scx{0.f, 0.f}, Scy{0.f, 0.f}, SU, Sth;
+  {
+    const DF l0 = df_mul(df_from_double_bits(s_lam[0][tid]), dfc(a.df_w_shell[0]));
+    SP = df_mul(l0, B00);
+    SU = df_mul(l0, dU0);
+    Sth = df_mul(l0, dT0);
+  }
+  // Every accumulated term is a cotangent times an O(1) polynomial value, so
+  // the 11-operation double-word additions keep the error at a few u^2 of the
+  // sum of the terms' magnitudes, as float64 accumulation does at n u.
+#pragma unroll
+  for (int j = 1; j < NSHELL; ++j) {
+    const DF c2 = dfc(a.df_c2_shell[j]);
+    const DF w = dfc(a.df_w_shell[j]);
+    const DF A0 = df_add_fast(df_mul(df_add_fast(df_mul(B02, c2), B01), c2), B00);
+    const DF A1 = df_add_fast(df_mul(B11, c2), B10);
+    const DF A2 = df_add_fast(df_mul(B21, c2), B20);
+    const DF aU = df_add_fast(df_mul(dU1, c2), dU0);                                 // dA0/dU2
+    const DF aT = df_add_fast(df_mul(df_add_fast(df_mul(dT2, c2), dT1), c2), dT0);  // dA0/dtheta
+    const DF hT = df_add(df_scale2(c2, 0.5f), -2.0f);                                // dA1/dtheta
+    const DF bT = df_add(df_scale2(c2, 0.25f), -1.5f);                               // dA2/dtheta
+    const DF A2x2 = df_scale2(A2, 2.0f);
+#pragma unroll 1
+    for (int k = shell_first_pair(j); k < shell_first_pair(j + 1); ++k) {
+      const float rx = (float)c_pair_rep[k][0], ry = (float)c_pair_rep[k][1];
+      const DF lp = df_from_double_bits(s_lam[2 * k + 1][tid]), lm = df_from_double_bits(s_lam[2 * k + 2][tid]);
+      const DF Ls = df_mul(df_add_fast(lp, lm), w), La = df_mul(df_add_fast(lp, df_neg(lm)), w);
+      const DF cu = df_add_fast(df_mul(v_x, rx), df_mul(v_y, ry));
+      const DF cu2 = df_mul(cu, cu);
+      const DF Pe = df_add_fast(df_mul(df_add_fast(df_mul(cu2, DF{0x1.555556p-5f, -0x1.555556p-30f}), A2), cu2), A0);
+      const DF P6 = df_mul(cu2, DF{0x1.555556p-3f, -0x1.555556p-28f});  // cu^2 / 6
+      const DF Po = df_mul(df_add_fast(P6, A1), cu);
+      const DF Pce = df_add_fast(df_scale2(cu2, 0.5f), A1);
+      const DF Pco = df_mul(df_add_fast(P6, A2x2), cu);
+      SP = df_add_fast(SP, df_add_fast(df_mul(Ls, Pe), df_mul(La, Po)));
+      const DF t = df_add_fast(df_mul(La, Pce), df_mul(Ls, Pco));
+      Scx = df_add_fast(Scx, df_mul(t, rx));
+      Scy = df_add_fast(Scy, df_mul(t, ry));
+      SU = df_add_fast(SU, df_add_fast(df_mul(Ls, df_add_fast(df_scale2(cu2, -0.25f), aU)),
+                                       df_mul(df_scale2(La, -0.5f), cu)));
+      Sth = df_add_fast(Sth, df_add_fast(df_mul(Ls, df_add_fast(df_mul(bT, cu2), aT)),
+                                         df_mul(df_mul(La, hT), cu)));
     }
   }
-  if (bottom) lam_out[scratch_idx(a, false, y, x)] = wall_sum;
-  if (top) lam_out[scratch_idx(a, true, a.ly - 1 - y, x)] = wall_sum;
+  EqCot s;
+  s.SP = df_to_double_bits(SP);
+  s.Scx = df_to_double_bits(Scx);
+  s.Scy = df_to_double_bits(Scy);
+  s.SU = df_to_double_bits(SU);
+  s.Sth = df_to_double_bits(Sth);
+  // the rest as adjoint_kernel, float64
+  const double vxd = a.r2 * sf.ux, vyd = a.r2 * (sf.uy - a.tau_g_xi);
+  const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
+  const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * vxd, s.SU, s.Scx));
+  const double gJy = a.r2 * fma(-s.Sth, sf.uy, fma(2.0 * a.inv_r2 * vyd, s.SU, s.Scy));
+  const double gE = 0.5 * a.r2 * s.Sth;
+  const double gR = s.SP - a.r2 * (sf.ux * (s.Scx + 2.0 * a.inv_r2 * vxd * s.SU) +
+                                   sf.uy * (s.Scy + 2.0 * a.inv_r2 * vyd * s.SU)) +
+                    s.Sth * fma(0.5 * a.r2, usq, -sf.T);
+  const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
+  double mu[NPOP];
+  mu[0] = fma(a.omc, s_lam[0][tid], wR);
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const double base = fma(wE, (double)shell_sq(pair_shell(k)), wR);
+    const double lin = pair_cu<double>(k, wJx, wJy);
+    mu[2 * k + 1] = fma(a.omc, s_lam[2 * k + 1][tid], base + lin);
+    mu[2 * k + 2] = fma(a.omc, s_lam[2 * k + 2][tid], base - lin);
+  }
+  push_cotangents(mu, x, y, a, lam_out);
 }
 
 // B^T for the populations that left through a wall: lam_out(l, y0, x) =
@@ -193,7 +317,9 @@ static dim3 site_grid(const LatticeArgs& a) {
 cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, double* lam_out, const LatticeArgs& a,
                            cudaStream_t s) {
   const dim3 grid = site_grid(a), block(ABX, ABY);
-  if (prec == LBM_FP64)
+  if (prec == LBM_FP64_DF)
+    adjoint_df_kernel<<<grid, block, 0, s>>>(static_cast<const double*>(f_t), lam_in, lam_out, a);
+  else if (prec == LBM_FP64)
     adjoint_kernel<LBM_FP64><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, a);
   else
     adjoint_kernel<LBM_FP32_SHIFTED><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, a);

@@ -347,7 +347,7 @@ int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const double* lam_in, double* 
     return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step: bad buffers");
   if (c->args.regularized)
     return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step: no adjoint of the regularised collide");
-  return cuda_check(c, launch_adjoint(storage_prec(c->p.precision), f_t, lam_in, lam_out, c->args, c->stream),
+  return cuda_check(c, launch_adjoint(c->p.precision, f_t, lam_in, lam_out, c->args, c->stream),
                     "lbm_adjoint_step");
 }
 

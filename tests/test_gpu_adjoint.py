@@ -50,12 +50,15 @@ def make(p, precision="fp64", rho0=1.0):
 
 @pytest.mark.parametrize("lx,ly", [(13, 10), (35, 7), (3, 6)])
 @pytest.mark.parametrize("periodic_y", [False, True])
-def test_adjoint_step_parity(lx, ly, periodic_y):
+@pytest.mark.parametrize("precision", ["fp64", "fp64df"])
+def test_adjoint_step_parity(lx, ly, periodic_y, precision):
+    # fp64df: the cotangent sums run in double-float (about 48 bits); the
+    # float64 bar holds for them too
     p = M.Params(lx, ly, tau=0.7, g=2e-3, t_top=0.85, t_bottom=1.2, periodic_y=periodic_y)
     f = noisy_state(lx, ly, 40 + lx)
     lam = rand_cot(lx, ly, 41 + ly)
     want = A.adjoint_step(f, lam, p)
-    lat = make(p)
+    lat = make(p, precision=precision)
     got = lat.adjoint_step(to_dev(f), to_dev(lam)).cpu().numpy()
     assert plane_err(got, want) <= 1e-12
 
