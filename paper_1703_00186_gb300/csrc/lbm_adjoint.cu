@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const double* __r
   // Every accumulated term is a cotangent times an O(1) polynomial value, so
   // the 11-operation double-word additions keep the error at a few u^2 of the
   // sum of the terms' magnitudes, as float64 accumulation does at n u.
-#pragma unroll
+  // Both loops are rolled: the unrolled body overflows the instruction cache.
+#pragma unroll 1
   for (int j = 1; j < NSHELL; ++j) {
     const DF c2 = dfc(a.df_c2_shell[j]);
     const DF w = dfc(a.df_w_shell[j]);
