@@ -227,16 +227,32 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const double* __r
                                    sf.uy * (s.Scy + 2.0 * a.inv_r2 * vyd * s.SU)) +
                     s.Sth * fma(0.5 * a.r2, usq, -sf.T);
   const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
-  double mu[NPOP];
-  mu[0] = fma(a.omc, s_lam[0][tid], wR);
-#pragma unroll
+  // mu_l = (1 - omega) lam_l + omega (gR + gJ . xi_l + gE |xi_l|^2), pushed
+  // back to its pull source as it is formed (P^T; wall slots reduce), in a
+  // loop rolled over the pairs: the same operations as adjoint_kernel
+  double wall_sum = 0.0;
+  auto push = [&](int l, int ex, int ey, double m) {
+    int ys = y - ey;
+    bool known = true;
+    if (a.periodic_y) {
+      ys = ys < 0 ? ys + a.ly : (ys >= a.ly ? ys - a.ly : ys);
+    } else if (ys < 0 || ys >= a.ly) {
+      known = false;
+    }
+    if (known) lam_out[sidx(a, l, ys, wrap_x(x - ex, a.lx))] = m;
+    else wall_sum = fma(ys < 0 ? a.q_bot[l] : a.q_top[l], m, wall_sum);
+  };
+  push(0, 0, 0, fma(a.omc, s_lam[0][tid], wR));
+#pragma unroll 1
   for (int k = 0; k < NPAIR; ++k) {
-    const double base = fma(wE, (double)shell_sq(pair_shell(k)), wR);
-    const double lin = pair_cu<double>(k, wJx, wJy);
-    mu[2 * k + 1] = fma(a.omc, s_lam[2 * k + 1][tid], base + lin);
-    mu[2 * k + 2] = fma(a.omc, s_lam[2 * k + 2][tid], base - lin);
+    const int rx = c_pair_rep[k][0], ry = c_pair_rep[k][1];
+    const double base = fma(wE, (double)(rx * rx + ry * ry), wR);
+    const double lin = fma((double)rx, wJx, (double)ry * wJy);  // = pair_cu(k, wJx, wJy) bit for bit
+    push(2 * k + 1, rx, ry, fma(a.omc, s_lam[2 * k + 1][tid], base + lin));
+    push(2 * k + 2, -rx, -ry, fma(a.omc, s_lam[2 * k + 2][tid], base - lin));
   }
-  push_cotangents(mu, x, y, a, lam_out);
+  if (!a.periodic_y && y < 3) lam_out[scratch_idx(a, false, y, x)] = wall_sum;
+  if (!a.periodic_y && y >= a.ly - 3) lam_out[scratch_idx(a, true, a.ly - 1 - y, x)] = wall_sum;
 }
 
 // B^T for the populations that left through a wall: lam_out(l, y0, x) =
