@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restri
   push_cotangents(mu, x, y, a, lam_out);
 }
 
+// The pair representatives R_k of c_pair_rep as float64: x, y and |R_k|^2.
+static __constant__ double c_pair_rep_d[NPAIR][3] = {
+    {1, 0, 1}, {0, 1, 1}, {1, 1, 2}, {-1, 1, 2}, {2, 0, 4}, {0, 2, 4}, {2, 1, 5}, {1, 2, 5}, {-1, 2, 5},
+    {-2, 1, 5}, {2, 2, 8}, {-2, 2, 8}, {3, 0, 9}, {0, 3, 9}, {3, 1, 10}, {1, 3, 10}, {-1, 3, 10}, {-3, 1, 10}};
+
 // Adjoint step of an LBM_FP64_DF context: the same transposed Jacobian with
 // the cotangent sums of the equilibrium in double-float arithmetic on the
 // FP32 pipe (as the forward collide of that mode), the pair loop rolled over
@@ -246,8 +251,10 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const double* __r
 #pragma unroll 1
   for (int k = 0; k < NPAIR; ++k) {
     const int rx = c_pair_rep[k][0], ry = c_pair_rep[k][1];
-    const double base = fma(wE, (double)(rx * rx + ry * ry), wR);
-    const double lin = fma((double)rx, wJx, (double)ry * wJy);  // = pair_cu(k, wJx, wJy) bit for bit
+    // float64 copies from a table: an int-to-double conversion would take an
+    // FP64 issue slot
+    const double base = fma(wE, c_pair_rep_d[k][2], wR);
+    const double lin = fma(c_pair_rep_d[k][0], wJx, c_pair_rep_d[k][1] * wJy);  // = pair_cu(k, wJx, wJy)
     push(2 * k + 1, rx, ry, fma(a.omc, s_lam[2 * k + 1][tid], base + lin));
     push(2 * k + 2, -rx, -ry, fma(a.omc, s_lam[2 * k + 2][tid], base - lin));
   }
