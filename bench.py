@@ -261,7 +261,8 @@ def rollout_study(steps, torch):
     """Checkpointed adjoint rollout on a 256 x 512 RT lattice: time of the
     forward rollout and of the backward sweep (recompute + adjoint steps),
     and the gradient against float64 central differences on 16 seeded
-    directions; FP64 and FP32-store."""
+    directions; FP64, FP32-store and FP64_DF (double-float collide and
+    cotangent sums)."""
     import numpy as np
 
     import synth
@@ -275,7 +276,7 @@ def rollout_study(steps, torch):
     rho_t, T_t, tgt = (torch.tensor(v, device=dev) for v in (rho, T, target))
     res = {"lattice": f"{lx}x{ly}", "steps": steps, "checkpoint_every": K, "tau": tau, "g": g}
     grads = {}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp64df"):
         lat = Lattice(lx, ly, tau=tau, g=g, t_top=tt, t_bottom=tb, precision=prec, rho0=float(rho.mean()))
         d = torch.tensor(dT0, device=dev, requires_grad=True)
         temperature_loss(d, lat, rho_t, T_t, tgt, 4, 2).backward()  # warm-up
@@ -309,8 +310,10 @@ def rollout_study(steps, torch):
             res["fp64"]["fd_eps"] = eps
         del lat
         torch.cuda.empty_cache()
-    g64, g32 = grads["fp64"], grads["fp32"]
-    res["fp32"]["grad_rel_diff_vs_fp64"] = float(np.abs(g32 - g64).max() / np.abs(g64).max())
+    g64 = grads["fp64"]
+    for prec in ("fp32", "fp64df"):
+        res[prec]["grad_rel_diff_vs_fp64"] = float(np.abs(grads[prec] - g64).max() / np.abs(g64).max())
+    res["fp64df"]["backward_over_fp64_forward"] = res["fp64df"]["backward_s"] / res["fp64"]["forward_s"]
     return res
 
 

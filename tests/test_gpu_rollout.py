@@ -83,3 +83,15 @@ def test_fp32_store_rollout_gradient_close_to_fp64():
     _, g64, _ = gpu_grad(p, rho, T, target, dT0, 40, 10, "fp64")
     _, g32, _ = gpu_grad(p, rho, T, target, dT0, 40, 10, "fp32")
     assert np.abs(g32 - g64).max() <= 1e-4 * np.abs(g64).max()
+
+
+def test_fp64df_rollout_gradient_matches_oracle_adjoint():
+    # double-float forward collide and cotangent sums (about 48 bits): the
+    # float64 gradient bar of the oracle comparison still holds
+    p, rho, T, target, dT0 = case(12, 16)
+    n = 9
+    J, g, _ = gpu_grad(p, rho, T, target, dT0, n, K=4, precision="fp64df")
+    Jo = A.rollout_loss(dT0, rho, T, target, p, n)
+    go = A.rollout_grad(dT0, rho, T, target, p, n)
+    assert J == pytest.approx(Jo, rel=1e-12)
+    assert np.abs(g - go).max() <= 1e-10 * np.abs(go).max()
