@@ -89,9 +89,7 @@ enum {
  *                    times the FP64 rate.  Propagate and bc are identical
  *                    (bit-exact); every other call treats the state as
  *                    LBM_FP64, except that lbm_adjoint_step evaluates the
- *                    equilibrium's cotangent sums in double-float too (the
- *                    transposed Jacobian of the float64 step, to about 48
- *                    bits). */
+ *                    equilibrium's cotangent sums in double-float too. */
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_DF = 2 };
 enum {
   LBM_FLAG_PERIODIC_Y = 1,   /* test mode: no walls, y periodic */
@@ -214,9 +212,12 @@ int lbm_propagate_bc(lbm_ctx* ctx, const void* src, void* dst);
  * eq. 1 with propagate, bc and collide, linearised at state f_t):
  *   lam_out = P^T B^T C^T lam_in.
  * f_t: state in the context's precision (FP32 states are decoded and the
- * Jacobian of the float64 step is taken there).  lam_in, lam_out: double
- * arrays in the FP64 state layout; must not alias.  The halo rows of lam_out
- * are used as scratch and hold no data afterwards. */
+ * Jacobian of the float64 step is taken there).  LBM_FP64 contexts evaluate
+ * it in float64; LBM_FP64_DF and LBM_FP32_SHIFTED contexts evaluate the
+ * equilibrium's cotangent sums in double-float (about 48 bits), the rest in
+ * float64.  lam_in, lam_out: double arrays in the FP64 state layout; must not
+ * alias.  The halo rows of lam_out are used as scratch and hold no data
+ * afterwards. */
 int lbm_adjoint_step(lbm_ctx* ctx, const void* f_t, const double* lam_in,
                      double* lam_out);
 

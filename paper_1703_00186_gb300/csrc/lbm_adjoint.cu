@@ -125,26 +125,35 @@ static __constant__ double c_pair_rep_d[NPAIR][3] = {
     {1, 0, 1}, {0, 1, 1}, {1, 1, 2}, {-1, 1, 2}, {2, 0, 4}, {0, 2, 4}, {2, 1, 5}, {1, 2, 5}, {-1, 2, 5},
     {-2, 1, 5}, {2, 2, 8}, {-2, 2, 8}, {3, 0, 9}, {0, 3, 9}, {3, 1, 10}, {1, 3, 10}, {-1, 3, 10}, {-3, 1, 10}};
 
-// Adjoint step of an LBM_FP64_DF context: the same transposed Jacobian with
+// Adjoint step of LBM_FP64_DF and LBM_FP32_SHIFTED contexts (the latter on
+// the decoded float64 state): the same transposed Jacobian with
 // the cotangent sums of the equilibrium in double-float arithmetic on the
 // FP32 pipe (as the forward collide of that mode), the pair loop rolled over
 // cotangents staged in shared memory; the site fields, the final cotangent
 // combination and the push stay float64.
 //   SP = sum lam w P,  Scu = sum lam w P_cu xi,  SU = sum lam w dP/dU2,
 //   Sth = sum lam w dP/dtheta (see eq_cotangent).
-__global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const double* __restrict__ src,
+template <int PREC>
+__global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const void* __restrict__ f_,
                                                                const double* __restrict__ lam_in,
                                                                double* __restrict__ lam_out, LatticeArgs a) {
+  using S = typename Dec<PREC>::T;
   __shared__ double s_lam[NPOP][ABX * ABY];
   const int x = blockIdx.x * ABX + threadIdx.x;
   const int y = blockIdx.y * ABY + threadIdx.y;
   if (x >= a.lx || y >= a.ly) return;
   const int tid = threadIdx.y * ABX + threadIdx.x;
-  Dec<LBM_FP64> dec{&a};
+  const S* __restrict__ src = static_cast<const S*>(f_);
+  Dec<PREC> dec{&a};
   SiteFields sf;
   {
     double f[NPOP];
-    pull(src, x, y, a, f);
+    {
+      S g[NPOP];
+      pull(src, x, y, a, g);
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) f[l] = dec(l, g[l]);
+    }
     walls(src, x, y, a, f, dec, [](int, double v) { return v; });
     sf = site_fields(site_moments([&](int l) { return f[l]; }), a);
   }
@@ -342,11 +351,11 @@ cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, doub
                            cudaStream_t s) {
   const dim3 grid = site_grid(a), block(ABX, ABY);
   if (prec == LBM_FP64_DF)
-    adjoint_df_kernel<<<grid, block, 0, s>>>(static_cast<const double*>(f_t), lam_in, lam_out, a);
+    adjoint_df_kernel<LBM_FP64><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, a);
   else if (prec == LBM_FP64)
     adjoint_kernel<LBM_FP64><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, a);
   else
-    adjoint_kernel<LBM_FP32_SHIFTED><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, a);
+    adjoint_df_kernel<LBM_FP32_SHIFTED><<<grid, block, 0, s>>>(f_t, lam_in, lam_out, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || a.periodic_y) return e;
   walls_adjoint_kernel<<<dim3((unsigned)((a.lx + 127) / 128), 2), 128, 0, s>>>(lam_out, a);
