@@ -602,7 +602,8 @@ __host__ __device__ constexpr int cpow(int v, int e) { return e == 0 ? 1 : v * c
 // xi_x^c xi_y^d and G the (block-diagonal) Gram matrix of the monomials; the
 // new populations are w_l R(xi_l) with R = omega rho P + (1 - omega) q, P the
 // equilibrium polynomial expanded in the same monomials.
-__device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const LatticeArgs& a) {
+// Monomial moments N (order N00 N20 N02 N40 N22 N04 N10 N30 N12 N01 N03 N21 N11 N31 N13).
+__device__ __forceinline__ void reg_moments_f64(const double (&f)[NPOP], double (&N)[15]) {
   double s[NPAIR], d[NPAIR];
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
@@ -625,6 +626,17 @@ __device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const Lattic
   const double N10 = Nm(1, 0), N30 = Nm(3, 0), N12 = Nm(1, 2);
   const double N01 = Nm(0, 1), N03 = Nm(0, 3), N21 = Nm(2, 1);
   const double N11 = Nm(1, 1), N31 = Nm(3, 1), N13 = Nm(1, 3);
+  N[0] = N00; N[1] = N20; N[2] = N02; N[3] = N40; N[4] = N22; N[5] = N04;
+  N[6] = N10; N[7] = N30; N[8] = N12; N[9] = N01; N[10] = N03; N[11] = N21;
+  N[12] = N11; N[13] = N31; N[14] = N13;
+}
+
+// The regularised collide's coefficients R of the new populations
+// f_l = w_l R(xi_l) from the monomial moments N (same order as N).
+__device__ __forceinline__ void reg_coefficients(const double (&N)[15], const LatticeArgs& a, double (&Rv)[15]) {
+  const double N00 = N[0], N20 = N[1], N02 = N[2], N40 = N[3], N22 = N[4], N04 = N[5];
+  const double N10 = N[6], N30 = N[7], N12 = N[8], N01 = N[9], N03 = N[10], N21 = N[11];
+  const double N11 = N[12], N31 = N[13], N13 = N[14];
   // site fields (rho, J, E are monomial moments)
   Moments mo;
   mo.rho = N00;
@@ -681,6 +693,16 @@ __device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const Lattic
   const double R10 = fma(wr, P10, om * qoe[0]), R30 = fma(wr, P30, om * qoe[1]), R12 = fma(wr, P12, om * qoe[2]);
   const double R01 = fma(wr, P01, om * qeo[0]), R03 = fma(wr, P03, om * qeo[1]), R21 = fma(wr, P21, om * qeo[2]);
   const double R11 = fma(wr, P11, om * qoo[0]), R31 = fma(wr, P31, om * qoo[1]), R13 = fma(wr, P13, om * qoo[2]);
+  Rv[0] = R00; Rv[1] = R20; Rv[2] = R02; Rv[3] = R40; Rv[4] = R22; Rv[5] = R04;
+  Rv[6] = R10; Rv[7] = R30; Rv[8] = R12; Rv[9] = R01; Rv[10] = R03; Rv[11] = R21;
+  Rv[12] = R11; Rv[13] = R31; Rv[14] = R13;
+}
+
+// f_l = w_l R(xi_l) for the coefficient vector R (same order as N).
+__device__ __forceinline__ void reg_reconstruct_f64(const double (&Rv)[15], const LatticeArgs& a, double (&f)[NPOP]) {
+  const double R00 = Rv[0], R20 = Rv[1], R02 = Rv[2], R40 = Rv[3], R22 = Rv[4], R04 = Rv[5];
+  const double R10 = Rv[6], R30 = Rv[7], R12 = Rv[8], R01 = Rv[9], R03 = Rv[10], R21 = Rv[11];
+  const double R11 = Rv[12], R31 = Rv[13], R13 = Rv[14];
   f[0] = a.w_shell[0] * R00;
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
@@ -705,6 +727,105 @@ __device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const Lattic
     const double wod = w * od;
     f[2 * k + 1] = fma(w, ev, wod);
     f[2 * k + 2] = fma(w, ev, -wod);
+  }
+}
+
+
+__device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const LatticeArgs& a) {
+  double N[15], Rv[15];
+  reg_moments_f64(f, N);
+  reg_coefficients(N, a, Rv);
+  reg_reconstruct_f64(Rv, a, f);
+}
+
+// xi_k^(c_i, e_i) for pair representative k and monomial i (order of N).
+static __constant__ signed char c_reg_coef[NPAIR][15] = {
+    {1, 1, 0, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0},
+    {1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 1, 0, 0, 0, 0},
+    {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {1, 1, 1, 1, 1, 1, -1, -1, -1, 1, 1, 1, -1, -1, -1},
+    {1, 4, 0, 16, 0, 0, 2, 8, 0, 0, 0, 0, 0, 0, 0},
+    {1, 0, 4, 0, 0, 16, 0, 0, 0, 2, 8, 0, 0, 0, 0},
+    {1, 4, 1, 16, 4, 1, 2, 8, 2, 1, 1, 4, 2, 8, 2},
+    {1, 1, 4, 1, 4, 16, 1, 1, 4, 2, 8, 2, 2, 2, 8},
+    {1, 1, 4, 1, 4, 16, -1, -1, -4, 2, 8, 2, -2, -2, -8},
+    {1, 4, 1, 16, 4, 1, -2, -8, -2, 1, 1, 4, -2, -8, -2},
+    {1, 4, 4, 16, 16, 16, 2, 8, 8, 2, 8, 8, 4, 16, 16},
+    {1, 4, 4, 16, 16, 16, -2, -8, -8, 2, 8, 8, -4, -16, -16},
+    {1, 9, 0, 81, 0, 0, 3, 27, 0, 0, 0, 0, 0, 0, 0},
+    {1, 0, 9, 0, 0, 81, 0, 0, 0, 3, 27, 0, 0, 0, 0},
+    {1, 9, 1, 81, 9, 1, 3, 27, 3, 1, 1, 9, 3, 27, 3},
+    {1, 1, 9, 1, 9, 81, 1, 1, 9, 3, 27, 3, 3, 3, 27},
+    {1, 1, 9, 1, 9, 81, -1, -1, -9, 3, 27, 3, -3, -3, -27},
+    {1, 9, 1, 81, 9, 1, -3, -27, -3, 1, 1, 9, -3, -27, -3}};
+
+__host__ __device__ constexpr bool reg_odd(int i) { return i >= 6 && i < 12; }
+
+// acc + c x for a small integer c read at run time (the same for the whole
+// warp, so the branches do not diverge).
+__device__ __forceinline__ Fix96 fix_axpy_rt(Fix96 acc, Fix96 x, int c) {
+  if (c == 0) return acc;
+  const unsigned m = (unsigned)(c < 0 ? -c : c);
+  const Fix96 t = m == 1u ? x : fix_mad(Fix96{0u, 0u, 0u}, x, m);
+  return c < 0 ? fix_sub(acc, t) : fix_add(acc, t);
+}
+
+// Regularised collide with its integer-weighted sums on the integer pipe:
+// the 15 monomial moments N and the even / odd parts of R(xi) for every pair
+// are exact 96-bit fixed-point sums (rounded once each), in loops rolled over
+// the pairs (populations staged in shared memory) so that fifteen
+// accumulators fit the register file; the coefficients R stay float64 and the
+// new populations w_l R(xi_l) go straight to dst.  Sites with a population
+// or a coefficient outside the fixed-point range take collide_fp64_reg.
+template <int NT>
+__device__ __forceinline__ void collide_fp64_reg_staged(const double (&f)[NPOP], const LatticeArgs& a,
+                                                        double (*s_f)[NT], int tid, double* __restrict__ dst,
+                                                        int x, int y) {
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) s_f[l][tid] = f[l];
+  bool ok = true;
+  double N[15];
+  {
+    Fix96 acc[15];
+    acc[0] = to_fix(s_f[0][tid], ok);
+#pragma unroll
+    for (int i = 1; i < 15; ++i) acc[i] = Fix96{0u, 0u, 0u};
+#pragma unroll 1
+    for (int k = 0; k < NPAIR; ++k) {
+      const Fix96 p = to_fix(s_f[2 * k + 1][tid], ok), m = to_fix(s_f[2 * k + 2][tid], ok);
+      const Fix96 sk = fix_add(p, m), dk = fix_sub(p, m);
+#pragma unroll
+      for (int i = 0; i < 15; ++i) acc[i] = fix_axpy_rt(acc[i], reg_odd(i) ? dk : sk, c_reg_coef[k][i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) N[i] = fix_to_double(acc[i]);
+  }
+  double Rv[15];
+  if (ok) reg_coefficients(N, a, Rv);
+  Fix96 X[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) X[i] = to_fix(ok ? Rv[i] : 0.0, ok);
+  if (!ok) {  // float64 path for this site
+    double g[NPOP];
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) g[l] = s_f[l][tid];
+    collide_fp64_reg(g, a);
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
+    return;
+  }
+  dst[sidx(a, 0, y, x)] = a.w_shell[0] * Rv[0];
+#pragma unroll 1
+  for (int k = 0; k < NPAIR; ++k) {
+    Fix96 ev = X[0], od{0u, 0u, 0u};
+#pragma unroll
+    for (int i = 1; i < 15; ++i) {
+      if (reg_odd(i)) od = fix_axpy_rt(od, X[i], c_reg_coef[k][i]);
+      else ev = fix_axpy_rt(ev, X[i], c_reg_coef[k][i]);
+    }
+    const double w = a.w_shell[pair_shell(k)];
+    dst[sidx(a, 2 * k + 1, y, x)] = w * fix_to_double(fix_add(ev, od));
+    dst[sidx(a, 2 * k + 2, y, x)] = w * fix_to_double(fix_sub(ev, od));
   }
 }
 

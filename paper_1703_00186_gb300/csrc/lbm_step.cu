@@ -63,10 +63,15 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const void* __restrict__ 
       return;
     }
   }
+  if constexpr (PREC == LBM_FP64 && REG) {
+    if (COLLIDE) {
+      __shared__ double s_f[NPOP][BX * BY];
+      collide_fp64_reg_staged<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
+      return;
+    }
+  }
   if (COLLIDE) {
-    if constexpr (PREC == LBM_FP64 && REG) {
-      collide_fp64_reg(f, a);
-    } else if constexpr (PREC == LBM_FP64) {
+    if constexpr (PREC == LBM_FP64) {
       collide_fp64(f, a);
     } else {
       collide_fp32(f, a);
