@@ -594,14 +594,6 @@ __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const Lattice
 
 __host__ __device__ constexpr int cpow(int v, int e) { return e == 0 ? 1 : v * cpow(v, e - 1); }
 
-// Regularised BGK collide in float64 (the Hermite projection of Sect. 2):
-//   f <- f^eq + (1 - omega) Pi(f - f^eq) = omega f^eq + (1 - omega) Pi f,
-// Pi the w-weighted projection onto the polynomials of degree <= 4 in the
-// velocity, which contain the equilibrium.  In integer-velocity monomials,
-// Pi f = w (sum_cd q_cd xi_x^c xi_y^d) with q = G^-1 N, N_cd = sum_l f_l
-// xi_x^c xi_y^d and G the (block-diagonal) Gram matrix of the monomials; the
-// new populations are w_l R(xi_l) with R = omega rho P + (1 - omega) q, P the
-// equilibrium polynomial expanded in the same monomials.
 // Monomial moments N (order N00 N20 N02 N40 N22 N04 N10 N30 N12 N01 N03 N21 N11 N31 N13).
 __device__ __forceinline__ void reg_moments_f64(const double (&f)[NPOP], double (&N)[15]) {
   double s[NPAIR], d[NPAIR];
@@ -730,7 +722,16 @@ __device__ __forceinline__ void reg_reconstruct_f64(const double (&Rv)[15], cons
   }
 }
 
-
+// Regularised BGK collide in float64 (the Hermite projection of Sect. 2):
+//   f <- f^eq + (1 - omega) Pi(f - f^eq) = omega f^eq + (1 - omega) Pi f,
+// Pi the w-weighted projection onto the polynomials of degree <= 4 in the
+// velocity, which contain the equilibrium.  In integer-velocity monomials,
+// Pi f = w (sum_cd q_cd xi_x^c xi_y^d) with q = G^-1 N, N_cd = sum_l f_l
+// xi_x^c xi_y^d and G the (block-diagonal) Gram matrix of the monomials; the
+// new populations are w_l R(xi_l) with R = omega rho P + (1 - omega) q, P the
+// equilibrium polynomial expanded in the same monomials.
+// This is the float64 evaluation; collide_fp64_reg_staged below forms the
+// integer-weighted sums in fixed point.
 __device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const LatticeArgs& a) {
   double N[15], Rv[15];
   reg_moments_f64(f, N);
