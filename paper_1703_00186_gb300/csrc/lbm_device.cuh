@@ -623,19 +623,11 @@ __device__ __forceinline__ void reg_moments_f64(const double (&f)[NPOP], double 
   N[12] = N11; N[13] = N31; N[14] = N13;
 }
 
-// The regularised collide's coefficients R of the new populations
-// f_l = w_l R(xi_l) from the monomial moments N (same order as N).
-__device__ __forceinline__ void reg_coefficients(const double (&N)[15], const LatticeArgs& a, double (&Rv)[15]) {
-  const double N00 = N[0], N20 = N[1], N02 = N[2], N40 = N[3], N22 = N[4], N04 = N[5];
-  const double N10 = N[6], N30 = N[7], N12 = N[8], N01 = N[9], N03 = N[10], N21 = N[11];
-  const double N11 = N[12], N31 = N[13], N13 = N[14];
-  // site fields (rho, J, E are monomial moments)
-  Moments mo;
-  mo.rho = N00;
-  mo.Jx = N10;
-  mo.Jy = N01;
-  mo.Exi = N20 + N02;
-  const SiteFields sf = site_fields(mo, a);
+// Coefficients P of the equilibrium polynomial (4th-order Hermite, with the
+// gravity shift) in the integer-velocity monomials of degree <= 4:
+// f^eq_l = w_l rho P(xi_l), P(xi) = sum_i P_i xi_x^(c_i) xi_y^(e_i), in the
+// order of N (expanded from cu = xi . v and c2 = r^2 |xi|^2).
+__device__ __forceinline__ void eq_monomials(const SiteFields& sf, const LatticeArgs& a, double (&P)[15]) {
   const double theta = sf.T + a.tshift;
   const double uys = sf.uy - a.tau_g_xi;
   const double vx_ = a.r2 * sf.ux, vy_ = a.r2 * uys;
@@ -659,6 +651,29 @@ __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const La
   const double P03 = vy_ * fma(B.B11, r2, vy2 * (1.0 / 6.0));
   const double P21 = vy_ * fma(B.B11, r2, vx2 * 0.5);
   const double P12 = vx_ * fma(B.B11, r2, vy2 * 0.5);
+  P[0] = P00; P[1] = P20; P[2] = P02; P[3] = P40; P[4] = P22; P[5] = P04;
+  P[6] = P10; P[7] = P30; P[8] = P12; P[9] = P01; P[10] = P03; P[11] = P21;
+  P[12] = P11; P[13] = P31; P[14] = P13;
+}
+
+// The regularised collide's coefficients R of the new populations
+// f_l = w_l R(xi_l) from the monomial moments N (same order as N).
+__device__ __forceinline__ void reg_coefficients(const double (&N)[15], const LatticeArgs& a, double (&Rv)[15]) {
+  const double N00 = N[0], N20 = N[1], N02 = N[2], N40 = N[3], N22 = N[4], N04 = N[5];
+  const double N10 = N[6], N30 = N[7], N12 = N[8], N01 = N[9], N03 = N[10], N21 = N[11];
+  const double N11 = N[12], N31 = N[13], N13 = N[14];
+  // site fields (rho, J, E are monomial moments)
+  Moments mo;
+  mo.rho = N00;
+  mo.Jx = N10;
+  mo.Jy = N01;
+  mo.Exi = N20 + N02;
+  const SiteFields sf = site_fields(mo, a);
+  double Pm[15];
+  eq_monomials(sf, a, Pm);
+  const double P00 = Pm[0], P20 = Pm[1], P02 = Pm[2], P40 = Pm[3], P22 = Pm[4], P04 = Pm[5];
+  const double P10 = Pm[6], P30 = Pm[7], P12 = Pm[8], P01 = Pm[9], P03 = Pm[10], P21 = Pm[11];
+  const double P11 = Pm[12], P31 = Pm[13], P13 = Pm[14];
   // projection coefficients q = G^-1 N, block by block
   const double* G = a.ginv;
   const double NE[6] = {N00, N20, N02, N40, N22, N04};
