@@ -363,7 +363,8 @@ def batch_study(steps, torch):
     shapes = Batch.tile_shapes()
     return {"lattices": len(b), "sites": b.sites, "steps": steps, "graph_launches": 1,
             "kernel_launches": steps, "ms": ms, "mlups": b.sites * steps / (ms * 1e-3) / 1e6,
-            "tile": shapes[best], "autotune_ms_per_step": {f"{bx}x{by}": t for (bx, by), t in zip(shapes, times)},
+            "tile": shapes[best],
+            "autotune_ms_per_step": {f"{bx}x{by}x{rows}": t for (bx, by, rows), t in zip(shapes, times)},
             "persistent": {"ms": ms_p, "mlups": b.sites * steps / (ms_p * 1e-3) / 1e6, "status": status_p,
                            "what": "one cooperative launch, grid barrier between steps, 32x4 tiles"},
             "lattices_finite_after": finite,

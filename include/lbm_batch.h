@@ -42,10 +42,12 @@ typedef struct lbm_lattice_desc {
 
 typedef struct lbm_batch lbm_batch;
 
-/* Number of tile shapes lbm_batch_autotune chooses from, and the shape of
- * candidate `i` (threads along x and y of a block; one site per thread). */
+/* Number of tile shapes lbm_batch_autotune chooses from, the block shape of
+ * candidate `i` (threads along x and y) and its sites per thread along y
+ * (a tile covers bx x (by * rows) sites; LBM_ERR_INVALID for a bad i). */
 int lbm_batch_tile_count(void);
 int lbm_batch_tile_shape(int i, int* bx, int* by);
+int lbm_batch_tile_rows(int i);
 
 /* Create a batch of n >= 1 lattices in `precision` (LBM_FP64 or
  * LBM_FP32_SHIFTED).  descs is a host array of n entries.  stream: cudaStream_t. */

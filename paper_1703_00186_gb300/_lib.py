@@ -78,6 +78,7 @@ SIGNATURES = {
     "lbm_probe_fma": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
     "lbm_batch_tile_count": (c_int, []),
     "lbm_batch_tile_shape": (c_int, [c_int, P(c_int), P(c_int)]),
+    "lbm_batch_tile_rows": (c_int, [c_int]),
     "lbm_batch_create": (c_int, [P(c_void_p), c_int, P(LbmLatticeDesc), c_int, c_void_p]),
     "lbm_batch_destroy": (None, [c_void_p]),
     "lbm_batch_last_error": (c_char_p, [c_void_p]),

@@ -76,12 +76,14 @@ class Batch:
 
     @staticmethod
     def tile_shapes():
+        """(threads along x, threads along y, sites per thread along y) of every
+        tile shape the autotuner chooses from."""
         lib = L.load()
         out = []
         for i in range(lib.lbm_batch_tile_count()):
             bx, by = ctypes.c_int(), ctypes.c_int()
             lib.lbm_batch_tile_shape(i, ctypes.byref(bx), ctypes.byref(by))
-            out.append((bx.value, by.value))
+            out.append((bx.value, by.value, lib.lbm_batch_tile_rows(i)))
         return out
 
     def set_tile(self, t: int):

@@ -37,9 +37,12 @@ struct BatchEntry {
 
 namespace {
 
-constexpr int kTiles = 6;
-constexpr int kTileBX[kTiles] = {32, 32, 64, 128, 32, 64};
-constexpr int kTileBY[kTiles] = {4, 8, 2, 1, 2, 4};
+constexpr int kTiles = 9;
+constexpr int kTileBX[kTiles] = {32, 32, 64, 128, 32, 64, 32, 32, 32};
+constexpr int kTileBY[kTiles] = {4, 8, 2, 1, 2, 4, 4, 4, 4};
+// sites per thread along y: a tile covers kTileBY * kTileRows rows, so the
+// per-tile work (lattice lookup, constants, barriers) is shared by more sites
+constexpr int kTileRows[kTiles] = {1, 1, 1, 1, 1, 1, 2, 4, 8};
 
 template <int PREC>
 struct BCodec;
@@ -60,7 +63,7 @@ struct BCodec<LBM_FP32_SHIFTED> {
 
 // One tile of the batch work list; block-wide: every thread of the block
 // calls it (threads outside the lattice skip the work but reach the barriers).
-template <int PREC, int TBX, int TBY, bool DFARITH, bool COHERENT>
+template <int PREC, int TBX, int TBY, bool DFARITH, bool COHERENT, int ROWS = 1>
 __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, const long long* __restrict__ tile_start,
                                            const int* __restrict__ tile_lattice, int parity, long long b,
                                            LatticeArgs& sa, const void*& s_src, void*& s_dst) {
@@ -83,7 +86,9 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
   const int tiles_x = (a.lx + TBX - 1) / TBX;
   const int ty = (int)(t / tiles_x), tx = (int)(t - (long long)ty * tiles_x);
   const int x = tx * TBX + threadIdx.x;
-  const int y = ty * TBY + threadIdx.y;
+#pragma unroll 1
+  for (int r = 0; r < ROWS; ++r) {
+  const int y = (ty * ROWS + r) * TBY + threadIdx.y;
   if (x < a.lx && y < a.ly) {
     const T* __restrict__ src = static_cast<const T*>(s_src);
     T* __restrict__ dst = static_cast<T*>(s_dst);
@@ -103,20 +108,21 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
       store_site(dst, x, y, a, f);
     }
   }
+  }
   __syncthreads();  // sa / s_src / s_dst are reused by the block's next tile
 }
 
 // FP32 tiles: at most 96 registers for 128-thread blocks (5 blocks per SM);
 // measured 5% faster than the unconstrained 128 registers, the small spill
 // included.
-template <int PREC, int TBX, int TBY, bool DFARITH = false>
+template <int PREC, int TBX, int TBY, bool DFARITH = false, int ROWS = 1>
 __global__ void __launch_bounds__(TBX * TBY, PREC == LBM_FP32_SHIFTED ? 5 * 128 / (TBX * TBY) : 0) batch_step_kernel(const BatchEntry* __restrict__ ent,
                                                                const long long* __restrict__ tile_start,
                                                                const int* __restrict__ tile_lattice, int parity) {
   __shared__ __align__(16) LatticeArgs sa;
   __shared__ const void* s_src;
   __shared__ void* s_dst;
-  batch_tile<PREC, TBX, TBY, DFARITH, false>(ent, tile_start, tile_lattice, parity, blockIdx.x, sa, s_src, s_dst);
+  batch_tile<PREC, TBX, TBY, DFARITH, false, ROWS>(ent, tile_start, tile_lattice, parity, blockIdx.x, sa, s_src, s_dst);
 }
 
 // Grid barrier of the persistent kernel with a bounded wait.  State in global
@@ -202,11 +208,11 @@ __global__ void barrier_selftest_kernel(GridBarrier* bar, unsigned long long bud
 template <int PREC, int I>
 cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long long* ts, const int* tl, int parity,
                           cudaStream_t s) {
-  constexpr int BX = kTileBX[I], BY = kTileBY[I];
+  constexpr int BX = kTileBX[I], BY = kTileBY[I], RW = kTileRows[I];
   if constexpr (PREC == LBM_FP64_DF)
-    batch_step_kernel<LBM_FP64, BX, BY, true><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, tl, parity);
+    batch_step_kernel<LBM_FP64, BX, BY, true, RW><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, tl, parity);
   else
-    batch_step_kernel<PREC, BX, BY><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, tl, parity);
+    batch_step_kernel<PREC, BX, BY, false, RW><<<(unsigned)blocks, dim3(BX, BY), 0, s>>>(ent, ts, tl, parity);
   return cudaGetLastError();
 }
 
@@ -219,7 +225,10 @@ cudaError_t launch_tile(int tile, long long blocks, const BatchEntry* ent, const
     case 2: return launch_tile_i<PREC, 2>(blocks, ent, ts, tl, parity, s);
     case 3: return launch_tile_i<PREC, 3>(blocks, ent, ts, tl, parity, s);
     case 4: return launch_tile_i<PREC, 4>(blocks, ent, ts, tl, parity, s);
-    default: return launch_tile_i<PREC, 5>(blocks, ent, ts, tl, parity, s);
+    case 5: return launch_tile_i<PREC, 5>(blocks, ent, ts, tl, parity, s);
+    case 6: return launch_tile_i<PREC, 6>(blocks, ent, ts, tl, parity, s);
+    case 7: return launch_tile_i<PREC, 7>(blocks, ent, ts, tl, parity, s);
+    default: return launch_tile_i<PREC, 8>(blocks, ent, ts, tl, parity, s);
   }
 }
 
@@ -332,6 +341,8 @@ int lbm_batch_tile_shape(int i, int* bx, int* by) {
   return LBM_OK;
 }
 
+int lbm_batch_tile_rows(int i) { return i < 0 || i >= kTiles ? LBM_ERR_INVALID : kTileRows[i]; }
+
 int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int precision, void* stream) {
   if (!out) return LBM_ERR_INVALID;
   *out = nullptr;
@@ -373,8 +384,9 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
   for (int t = 0; t < kTiles; ++t) {
     std::vector<long long> ts(n + 1, 0);
     for (int i = 0; i < n; ++i) {
+      const int rows = kTileBY[t] * kTileRows[t];
       const long long tiles = (long long)((b->args[i].lx + kTileBX[t] - 1) / kTileBX[t]) *
-                              ((b->args[i].ly + kTileBY[t] - 1) / kTileBY[t]);
+                              ((b->args[i].ly + rows - 1) / rows);
       ts[i + 1] = ts[i] + tiles;
     }
     b->blocks[t] = ts[n];

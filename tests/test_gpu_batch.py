@@ -56,7 +56,13 @@ def oracle_run(spec, f, n):
     return M.run(M.init_state(*f), p, n)
 
 
-@pytest.mark.parametrize("tile", range(6))
+def test_tile_shapes():
+    shapes = Batch.tile_shapes()
+    assert len(shapes) == 9
+    assert all(bx * by <= 256 and rows >= 1 for bx, by, rows in shapes)
+
+
+@pytest.mark.parametrize("tile", range(9))
 def test_batch_fp64_matches_oracle_for_every_tile_shape(tile):
     specs, flds = build("fp64")
     b = Batch(specs, precision="fp64")
