@@ -366,7 +366,7 @@ def batch_study(steps, torch):
             "tile": shapes[best],
             "autotune_ms_per_step": {f"{bx}x{by}x{rows}": t for (bx, by, rows), t in zip(shapes, times)},
             "persistent": {"ms": ms_p, "mlups": b.sites * steps / (ms_p * 1e-3) / 1e6, "status": status_p,
-                           "what": "one cooperative launch, grid barrier between steps, 32x4 tiles"},
+                           "what": "one cooperative launch, grid barrier between steps, 32x4 blocks x 8 rows"},
             "lattices_finite_after": finite,
             "state_bytes": 2 * 37 * 4 * sum(sp.lx * (sp.ly + 6) for sp in specs)}
 

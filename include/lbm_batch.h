@@ -75,7 +75,8 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* best, double* times_ms);
 int lbm_batch_step(lbm_batch* b, int n);
 
 /* Advance every lattice by n >= 0 steps with ONE persistent cooperative
- * launch: blocks stride over the tile list (32 x 4 tiles) and meet at a grid
+ * launch: blocks stride over the tile list (32 x 4 blocks, 8 rows per
+ * thread) and meet at a grid
  * barrier between steps.  Every barrier wait is bounded (2 s of global time or
  * 2^24 polls); if a wait gives up, the kernel sets a status flag and all
  * blocks return, and lbm_batch_status() reports LBM_ERR_TIMEOUT.  Same

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128, PREC == LBM_FP32_SHIFTED ? 5 : 0) batch_p
   for (int st = 0; st < steps; ++st) {
     const int parity = (parity0 + st) & 1;
     for (long long b = blockIdx.x; b < tiles; b += gridDim.x)
-      batch_tile<PREC, 32, 4, DFARITH, true>(ent, tile_start, tile_lattice, parity, b, sa, s_src, s_dst);
+      batch_tile<PREC, 32, 4, DFARITH, true, 8>(ent, tile_start, tile_lattice, parity, b, sa, s_src, s_dst);
     if (st + 1 < steps && !grid_barrier(bar, gridDim.x, budget_ns)) return;
   }
 }
@@ -538,13 +538,13 @@ int launch_persistent(lbm_batch* b, int n, unsigned long long budget_ns) {
   if (!rc) rc = bcuda(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0), "persistent step");
   if (rc) return rc;
   if (!coop || per_sm < 1) return bfail(b, LBM_ERR_INVALID, "persistent step: cooperative launch unavailable");
-  const long long tiles = b->blocks[0];  // the 32 x 4 tiling
+  const long long tiles = b->blocks[8];  // the 32 x 4 x 8 tiling
   const unsigned int grid = (unsigned int)std::min<long long>((long long)per_sm * sms, tiles);
   rc = bcuda(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream), "persistent step");
   if (rc) return rc;
   const BatchEntry* ent = b->d_ent;
-  const long long* ts = b->d_tiles[0];
-  const int* tl = b->d_tile_lat[0];
+  const long long* ts = b->d_tiles[8];
+  const int* tl = b->d_tile_lat[8];
   int parity = b->parity, steps = n;
   GridBarrier* bar = b->d_bar;
   void* args[] = {(void*)&ent, (void*)&ts, (void*)&tl, (void*)&tiles, (void*)&parity, (void*)&steps, (void*)&bar,
