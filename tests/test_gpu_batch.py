@@ -149,3 +149,17 @@ def test_bounded_barrier_wait_times_out_and_batch_stays_usable():
     assert b.status() == 0
     for i, s in enumerate(specs):
         assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, flds[i], 3)) <= 1e-12
+
+
+@pytest.mark.parametrize("tile", [0, 8])
+def test_batch_fp64df_matches_oracle(tile):
+    # float64 storage with the double-float collide, graph and persistent launches
+    specs, flds = build("fp64df")
+    b = Batch(specs, precision="fp64df")
+    b.set_tile(tile)
+    for i, f in enumerate(flds):
+        b.init(i, *f)
+    b.step(2).step_persistent(2)
+    assert b.status() == 0
+    for i, (s, f) in enumerate(zip(specs, flds)):
+        assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, f, 4)) <= 1e-12, i
