@@ -12,8 +12,8 @@ fp32_store   the same lattice stored as float32 deviations f_l - w_l rho0.
 adjoint      one adjoint step (recompute + transposed collide + push) over
              the same lattice, as a ratio to the forward step time.
 e2e          the same metric through the C ABI with pinned HOST buffers:
-             per step set_state(host) -> step -> get_state(host), two
-             independent lattices on two streams.
+             per step set_state(host) -> step -> get_state(host), three
+             independent lattices on their own streams.
 roofline     the fused float64 kernel against the FP64 FMA rate measured by
              the library's probe (the step is FP64-pipe bound).
 cpu_baseline the float64 oracle (NumPy) on a bounded sample of the workload.
@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--lx", type=int, default=2048)
     ap.add_argument("--ly", type=int, default=4096)
     ap.add_argument("--only", default="", help="comma list of sections: " + ",".join(SECTIONS))
+    ap.add_argument("--e2e-lattices", type=int, default=3,
+                    help="independent lattices (one stream each) in the end-to-end measurement")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--error-steps", type=int, default=1000)
     ap.add_argument("--rollout-steps", type=int, default=2000)
@@ -549,11 +551,11 @@ def main():
         out["adjoint"]["fp64df"] = {"adjoint_ms_per_step": ta_df, "forward_ms_per_step": tf_df,
                                     "ratio": ta_df / tf_df, "ratio_vs_fp64_forward": ta_df / tf_ms}
     if "e2e" in only:
-        # Two independent lattices, each on its own stream, each step of each
+        # Independent lattices, each on its own stream, each step of each
         # lattice through the C ABI from and to pinned host memory:
         # set_state(host) -> step(1) -> get_state(host).  The copy engines
-        # move one lattice's state in while the other's goes out or computes.
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        # move one lattice's state in while another's goes out or computes.
+        streams = [torch.cuda.Stream() for _ in range(args.e2e_lattices)]
         lats = [rt_lattice(lx, ly, "fp64", stream=st)[0] for st in streams]
         host_in = [torch.empty(lats[0].shape, dtype=lats[0].dtype, pin_memory=True) for _ in lats]
         host_out = [torch.empty(lats[0].shape, dtype=lats[0].dtype, pin_memory=True) for _ in lats]
@@ -572,13 +574,15 @@ def main():
         barrier(torch, world)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        eb = torch.cuda.Event()
         e0.record(streams[0])
-        streams[1].wait_event(e0)
+        for st in streams[1:]:
+            st.wait_event(e0)
         for _ in range(ke):
             e2e_round()
-        eb.record(streams[1])
-        streams[0].wait_event(eb)
+        for st in streams[1:]:
+            eb = torch.cuda.Event()
+            eb.record(st)
+            streams[0].wait_event(eb)
         e1.record(streams[0])
         e1.synchronize()
         te = dist_max(e0.elapsed_time(e1), torch, world)
@@ -586,7 +590,7 @@ def main():
                       "h2d_bytes_per_step": lats[0].nbytes, "d2h_bytes_per_step": lats[0].nbytes,
                       "steps": ke * len(lats), "lattices": len(lats),
                       "path": "per lattice step: lbm_set_state(pinned host) + lbm_step(1) + "
-                              "lbm_get_state(pinned host); two lattices on two streams"}
+                              "lbm_get_state(pinned host); independent lattices on their own streams"}
         del lats, host_in, host_out
         torch.cuda.empty_cache()
     if "fp32_error" in only:
