@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restri
   double lam[NPOP];
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) lam[l] = __ldg(lam_in + sidx(a, l, y, x));
-  const EqCot s = eq_cotangent([&](int l) { return lam[l]; }, v_x, v_y, U2, theta, a);
+  const EqCot s = eq_cotangent_mono([&](int l) { return lam[l]; }, v_x, v_y, U2, theta, a);
   // gamma_q = sum_m lam_m d f^eq_m / d q for q = rho, Jx, Jy, Exi (xi units)
   const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
   const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * v_x, s.SU, s.Scx));
