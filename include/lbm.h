@@ -33,15 +33,15 @@
  * above the ly physical rows), each row lx elements, x fastest:
  *     f[(l * (ly + 6) + (y + 3)) * lx + x]
  * (the structure-of-arrays layout of Sect. 4, Fig. "streamscheme").
- * Element type: double (LBM_FP64), or float holding f_l - w_l rho0
- * (LBM_FP32_SHIFTED).  Halo rows are never read as data and never written
+ * Element type: double (LBM_FP64, LBM_FP64_DF), or float holding
+ * f_l - w_l rho0 (LBM_FP32_SHIFTED).  Halo rows are never read as data and never written
  * by a step: they may hold anything, NaN included.
  * Macroscopic fields are double arrays of ly rows of lx, x fastest.
  *
  * OWNERSHIP.  The caller owns every lattice and field buffer (device memory
  * unless stated otherwise) and the CUDA stream.  A context allocates one
  * small device block of its own (status word and flags, freed by
- * lbm_destroy); a batch additionally allocates its small parameter table.
+ * lbm_destroy); a batch allocates its own tables (include/lbm_batch.h).
  * All work is enqueued asynchronously on the context's stream; a call
  * returns once its work is enqueued.
  *
