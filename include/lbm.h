@@ -191,8 +191,9 @@ int lbm_profiles(lbm_ctx* ctx, const void* f, double* out);
  * (steps every, 2 every, ...) store the row averages of the new state in the
  * next record of `out` (device double array [n / every][LBM_NOBS][ly]).  The
  * observing steps compute the averages in the step kernel itself from the
- * moments the collide already forms (summation order across warps is not
- * fixed: results agree with lbm_profiles to rounding).  LBM_FP64 contexts
+ * moments the collide already forms (exact warp sums, then one atomic add
+ * per warp and quantity, so the order across warps is not fixed: results
+ * agree with lbm_profiles to rounding).  LBM_FP64 contexts
  * without LBM_FLAG_REGULARIZED only; every >= 1.  *records (host, may be NULL)
  * receives the number of records written. */
 int lbm_step_observe(lbm_ctx* ctx, int n, int every, double* out, int* records);
