@@ -210,12 +210,25 @@ __device__ __forceinline__ bool moment_sums_exact(Get get, Moments& mo) {
 }
 
 // Moment sums of 37 float64 values: exact (moment_sums_exact) where the
-// populations fit the fixed-point range, float64 additions (moment_sums)
-// otherwise, so that infinities and NaNs still propagate.
+// populations fit the fixed-point range, float64 additions (moment_sums) for
+// finite populations beyond it, and NaN moments for a site holding an
+// infinity or a NaN (so a diverged state stays non-finite, at the cost of
+// the normal path).
 template <typename Get>
 __device__ __forceinline__ Moments site_moments(Get get) {
   Moments mo;
-  if (!moment_sums_exact(get, mo)) mo = moment_sums(get);
+  if (!moment_sums_exact(get, mo)) {
+    bool nonfinite = false;
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l)
+      nonfinite |= ((unsigned)__double2hiint(get(l)) & 0x7ff00000u) == 0x7ff00000u;
+    if (nonfinite) {
+      const double q = __longlong_as_double(0x7ff8000000000000LL);
+      mo = Moments{q, q, q, q};
+    } else {
+      mo = moment_sums(get);
+    }
+  }
   return mo;
 }
 

@@ -449,3 +449,27 @@ def test_fp32_step_path_falls_back_to_plain_loads():
     assert Lattice(64, 12, periodic_y=True, **kw).step_path() == "plain"   # y wraps
     assert Lattice(64, 12, tau=0.7, tma_loads=True).step_path() == "plain"  # float64 modes
     assert Lattice(64, 12, tau=0.7, precision="fp32").step_path() == "plain"  # not requested
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64df"])
+def test_non_finite_population_stays_local_and_non_finite(precision):
+    # An infinite population makes its site's moments non-finite (NaN); after
+    # one step exactly the sites that pull from it, or from the same column
+    # sums, are non-finite, as in the oracle, and every other site still
+    # matches the oracle.
+    lx, ly = 24, 20
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.9, t_bottom=1.1)
+    f = noisy_state(lx, ly, 95)
+    f[7, 3 + 10, 12] = np.inf
+    with np.errstate(invalid="ignore", over="ignore"):
+        want = M.step(f, p)
+    lat = make(p, precision=precision)
+    lat.set_state(to_dev(f))
+    lat.step(1)
+    got = lat.state().cpu().numpy()
+    gw, ww = M.physical(got), M.physical(want)
+    fin = np.isfinite(ww).all(axis=0)
+    assert (~fin).any()
+    np.testing.assert_array_equal(np.isfinite(gw).all(axis=0), fin)
+    scale = np.abs(ww[:, fin]).max(axis=1)
+    assert (np.abs(gw[:, fin] - ww[:, fin]).max(axis=1) / scale).max() <= 1e-12
