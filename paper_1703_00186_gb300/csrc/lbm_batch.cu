@@ -104,7 +104,7 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
       if constexpr (PREC == LBM_FP64)
         collide_fp64(f, a);
       else
-        collide_fp32(f, a);
+        collide_fp32<!COHERENT>(f, a);  // the persistent kernel keeps the scalar relaxation
       store_site(dst, x, y, a, f);
     }
   }
@@ -112,11 +112,11 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
   __syncthreads();  // sa / s_src / s_dst are reused by the block's next tile
 }
 
-// FP32 tiles: at most 96 registers for 128-thread blocks (5 blocks per SM);
-// measured 5% faster than the unconstrained 128 registers, the small spill
-// included.
+// FP32 tiles: at most 128 registers for 128-thread blocks (4 blocks per SM).
+// With the packed relaxation a 96-register cap spilled 124-140 bytes and
+// measured 10% slower.
 template <int PREC, int TBX, int TBY, bool DFARITH = false, int ROWS = 1>
-__global__ void __launch_bounds__(TBX * TBY, PREC == LBM_FP32_SHIFTED ? 5 * 128 / (TBX * TBY) : 0) batch_step_kernel(const BatchEntry* __restrict__ ent,
+__global__ void __launch_bounds__(TBX * TBY, PREC == LBM_FP32_SHIFTED ? 4 * 128 / (TBX * TBY) : 0) batch_step_kernel(const BatchEntry* __restrict__ ent,
                                                                const long long* __restrict__ tile_start,
                                                                const int* __restrict__ tile_lattice, int parity) {
   __shared__ __align__(16) LatticeArgs sa;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "dfloat.cuh"
+#include "f32x2.cuh"
 #include "fixed96.cuh"
 #include "lbm_internal.h"
 
@@ -345,36 +346,41 @@ __device__ __forceinline__ Split split2(float v) {
 // the 2^-34-grid parts exactly as integers.  The only error is the rounding
 // of each d_l to the 2^-34 grid: at most 2^-35 per term, round-to-nearest and
 // so without bias, three orders of magnitude below the float32 quantum of the
-// stored deviations.  Population pairs (2k+1, 2k+2) = (R_k, -R_k) are
-// combined first: the even moments take d+ + d-, the odd ones d+ - d-.
+// stored deviations.  Population pairs (2k+1, 2k+2) = (R_k, -R_k) are split
+// together in the two lanes of packed float32 pairs, and each h sum is kept
+// as one partial sum per lane (every partial sum is exact, so is their total);
+// the integer parts combine the pair first: the even moments take m+ + m-,
+// the odd ones m+ - m-.
 __device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
   constexpr unsigned K2 = 0x3a400000u;  // bit pattern of 1.5 * 2^-11
+  const float2 C1 = f2s(3072.0f), C1n = f2s(-3072.0f), C2 = f2s(0x1.8p-11f);
   const Split s0 = split2(d[0]);
-  SplitAcc r{s0.h, s0.bits}, jx{0.f, 0u}, jy{0.f, 0u}, e{0.f, 0u};
-  unsigned e_off = 0u;
+  float2 r2 = f2(s0.h, 0.f), e2 = f2(0.f, 0.f), jx2 = f2(0.f, 0.f), jy2 = f2(0.f, 0.f);
+  unsigned rm = s0.bits, em = 0u, jxm = 0u, jym = 0u, e_off = 0u;
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
-    const Split p = split2(d[2 * k + 1]);
-    const Split q = split2(d[2 * k + 2]);
-    const float sh = p.h + q.h, dh = p.h - q.h;      // exact: 2^-12 grid, < 2^12
-    const unsigned sm = p.bits + q.bits, dm = p.bits - q.bits;
-    const int c2 = rep_x(k) * rep_x(k) + rep_y(k) * rep_y(k);
-    r.h += sh;
-    r.m += sm;
-    e.h = fmaf((float)c2, sh, e.h);
-    e.m += (unsigned)c2 * sm;
+    const float2 v = f2(d[2 * k + 1], d[2 * k + 2]);
+    const float2 h = add2(add2(v, C1), C1n);  // both lanes of split2
+    const float2 t = add2(sub2(v, h), C2);
+    const unsigned pb = __float_as_uint(t.x), qb = __float_as_uint(t.y);
+    const unsigned sm = pb + qb, dm = pb - qb;
+    const int ax = rep_x(k), ay = rep_y(k), c2 = ax * ax + ay * ay;
+    r2 = add2(r2, h);
+    rm += sm;
+    e2 = c2 == 1 ? add2(e2, h) : fma2(f2s((float)c2), h, e2);
+    em += (unsigned)c2 * sm;
     e_off += 2u * (unsigned)c2;
-    if (rep_x(k) != 0) {
-      jx.h = fmaf((float)rep_x(k), dh, jx.h);
-      jx.m += (unsigned)rep_x(k) * dm;
+    if (ax != 0) {
+      jx2 = fma2(f2((float)ax, (float)-ax), h, jx2);
+      jxm += (unsigned)ax * dm;
     }
-    if (rep_y(k) != 0) {
-      jy.h = fmaf((float)rep_y(k), dh, jy.h);
-      jy.m += (unsigned)rep_y(k) * dm;
+    if (ay != 0) {
+      jy2 = fma2(f2((float)ay, (float)-ay), h, jy2);
+      jym += (unsigned)ay * dm;
     }
   }
-  r.m -= (unsigned)NPOP * K2;
-  e.m -= e_off * K2;
+  const SplitAcc r{r2.x + r2.y, rm - (unsigned)NPOP * K2}, e{e2.x + e2.y, em - e_off * K2};
+  const SplitAcc jx{jx2.x + jx2.y, jxm}, jy{jy2.x + jy2.y, jym};
   return {split_result(r), split_result(jx), split_result(jy), split_result(e)};
 }
 
@@ -458,6 +464,9 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 // conserved moments of the new populations are therefore measured again and
 // the small defect is put back on the rest and |xi| = 1 populations, so the
 // collide conserves mass and energy and adds exactly rho g to the momentum.
+// PAIRED relaxes each (+, -) pair with one packed FMA (fewer issue slots, a few
+// more live registers); the results are identical either way.
+template <bool PAIRED = true>
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
   MomentsDF dev;
   float rf = 0.f;
@@ -509,8 +518,14 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
         const float cu2 = cu * cu;
         const float E = fmaf(alpha * cu2, fmaf(cu2, 1.0f / 24.0f, A2), beta);
         const float O = alpha * cu * fmaf(cu2, 1.0f / 6.0f, A1);
-        d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
-        d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
+        if constexpr (PAIRED) {
+          const float2 D = fma2(f2s(omc), f2(d[2 * k + 1], d[2 * k + 2]), f2(E + O, E - O));
+          d[2 * k + 1] = D.x;
+          d[2 * k + 2] = D.y;
+        } else {
+          d[2 * k + 1] = fmaf(omc, d[2 * k + 1], E + O);
+          d[2 * k + 2] = fmaf(omc, d[2 * k + 2], E - O);
+        }
       }
     } else {
       // conserved-moment correction.  Targets of the exact BGK update with
