@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--error-steps", type=int, default=1000)
     ap.add_argument("--rollout-steps", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--batch-lattices", type=int, default=64)
+    ap.add_argument("--batch-tile", type=int, default=-1,
+                    help="batch tile shape index (default: autotune over all shapes)")
     return ap.parse_args()
 
 
@@ -319,12 +322,12 @@ def rollout_study(steps, torch):
     return res
 
 
-def batch_study(steps, torch):
+def batch_study(steps, torch, lattices=64, tile=-1):
     """64 independent RT lattices of uneven sizes and parameters, FP32-store,
     autotuned tile, `steps` steps as one CUDA-graph launch."""
     import synth
     from paper_1703_00186_gb300.batch import Batch
-    specs = synth.batch_lattices(64, 7)
+    specs = synth.batch_lattices(lattices, 7)
     flds, descs = [], []
     for sp in specs:
         rho, ux, uy, T, tt, tb = synth.rt_fields(sp.lx, sp.ly, 8, sp.seed, delta=sp.delta)
@@ -333,7 +336,11 @@ def batch_study(steps, torch):
     b = Batch(descs, precision="fp32")
     for i, f in enumerate(flds):
         b.init(i, *f)
-    best, times = b.autotune(steps=3)
+    if tile < 0:
+        best, times = b.autotune(steps=3)
+    else:
+        b.set_tile(tile)
+        best, times = tile, []
     for i, f in enumerate(flds):
         b.init(i, *f)
     b.step(steps)          # capture the graph once (untimed) ...
@@ -600,7 +607,7 @@ def main():
         out["rollout"] = rollout_study(args.rollout_steps, torch)
         torch.cuda.empty_cache()
     if "batch" in only:
-        out["batch"] = batch_study(args.batch_steps, torch)
+        out["batch"] = batch_study(args.batch_steps, torch, args.batch_lattices, args.batch_tile)
         torch.cuda.empty_cache()
     barrier(torch, world)
     if rank != 0:
