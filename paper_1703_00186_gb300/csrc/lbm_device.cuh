@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "dfloat.cuh"
+#include "dfloat_x2.cuh"
 #include "f32x2.cuh"
 #include "fixed96.cuh"
 #include "lbm_internal.h"
@@ -555,6 +556,15 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
 static __constant__ signed char c_pair_rep[NPAIR][2] = {
     {1, 0}, {0, 1}, {1, 1}, {-1, 1}, {2, 0}, {0, 2}, {2, 1}, {1, 2}, {-1, 2},
     {-2, 1}, {2, 2}, {-2, 2}, {3, 0}, {0, 3}, {3, 1}, {1, 3}, {-1, 3}, {-3, 1}};
+// The same representatives for pairs 2g and 2g+1 side by side, as float32
+// lane pairs with their negations: rx, -rx, ry, -ry.
+#define LBM_REP_X2(g)                                                                          \
+  {(float)rep_x(2 * (g)), (float)rep_x(2 * (g) + 1), (float)-rep_x(2 * (g)), (float)-rep_x(2 * (g) + 1), \
+   (float)rep_y(2 * (g)), (float)rep_y(2 * (g) + 1), (float)-rep_y(2 * (g)), (float)-rep_y(2 * (g) + 1)}
+static __constant__ float c_pair_rep_x2[NPAIR / 2][8] = {LBM_REP_X2(0), LBM_REP_X2(1), LBM_REP_X2(2),
+                                                         LBM_REP_X2(3), LBM_REP_X2(4), LBM_REP_X2(5),
+                                                         LBM_REP_X2(6), LBM_REP_X2(7), LBM_REP_X2(8)};
+#undef LBM_REP_X2
 // first pair of shell j (j = 1..7), and one past the last
 __host__ __device__ constexpr int shell_first_pair(int j) {
   return j == 1 ? 0 : j == 2 ? 2 : j == 3 ? 4 : j == 4 ? 6 : j == 5 ? 10 : j == 6 ? 12 : j == 7 ? 14 : 18;
@@ -594,6 +604,9 @@ __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const Lattice
   const DF B02 = df_scale2(th2, 0.125f);
   const DF wr = df_mul(rho, dfc(a.df_omega));
   dst[sidx(a, 0, y, x)] = fma(a.omc, f[0], df_to_double_bits(df_mul(df_mul(wr, dfc(a.df_w_shell[0])), B00)));
+  const DF2 VX = df2_bcast(v_x), VY = df2_bcast(v_y);
+  const DF2 C24 = df2_bcast(DF{0x1.555556p-5f, -0x1.555556p-30f}), C6 = df2_bcast(DF{0x1.555556p-3f, -0x1.555556p-28f});
+  const float2 nC24 = f2s(-0x1.555556p-5f), nC6 = f2s(-0x1.555556p-3f);  // 1/24, 1/6
 #pragma unroll
   for (int j = 1; j < NSHELL; ++j) {
     // Every sum below ends up in sc (E +- O) with E = A0 + O(cu^2) and
@@ -605,17 +618,29 @@ __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const Lattice
     const DF A1 = df_add_fast(df_mul(B11, c2), B10);
     const DF A2 = df_add_fast(df_mul(B21, c2), B20);
     const DF sc = df_mul(wr, dfc(a.df_w_shell[j]));
+    const DF2 A0v = df2_bcast(A0), A1v = df2_bcast(A1), A2v = df2_bcast(A2), scv = df2_bcast(sc);
+    const float2 nsc = f2s(-sc.hi);
+    // two pairs of the shell per iteration, one in each lane (every shell
+    // holds an even number of pairs)
 #pragma unroll 1
-    for (int k = shell_first_pair(j); k < shell_first_pair(j + 1); ++k) {
-      const float rx = (float)c_pair_rep[k][0], ry = (float)c_pair_rep[k][1];
-      const DF cu = df_add_fast(df_mul(v_x, rx), df_mul(v_y, ry));
-      const DF cu2 = df_mul(cu, cu);
-      const DF E = df_add_fast(df_mul(df_add_fast(df_mul(cu2, DF{0x1.555556p-5f, -0x1.555556p-30f}), A2), cu2), A0);  // 1/24
-      const DF O = df_mul(df_add_fast(df_mul(cu2, DF{0x1.555556p-3f, -0x1.555556p-28f}), A1), cu);               // 1/6
-      const DF sE = df_mul(sc, E), sO = df_mul(sc, O);
-      const int lp = 2 * k + 1, lm = 2 * k + 2;
-      dst[sidx(a, lp, y, x)] = fma(a.omc, s_f[lp][tid], df_to_double_bits(df_add_fast(sE, sO)));
-      dst[sidx(a, lm, y, x)] = fma(a.omc, s_f[lm][tid], df_to_double_bits(df_add_fast(sE, df_neg(sO))));
+    for (int g = shell_first_pair(j) / 2; g < shell_first_pair(j + 1) / 2; ++g) {
+      const float2 rx = f2(c_pair_rep_x2[g][0], c_pair_rep_x2[g][1]);
+      const float2 nrx = f2(c_pair_rep_x2[g][2], c_pair_rep_x2[g][3]);
+      const float2 ry = f2(c_pair_rep_x2[g][4], c_pair_rep_x2[g][5]);
+      const float2 nry = f2(c_pair_rep_x2[g][6], c_pair_rep_x2[g][7]);
+      const DF2 cu = df2_add_fast(df2_mul_f(VX, rx, nrx), df2_mul_f(VY, ry, nry));
+      const float2 ncu = df2_neg_hi(cu);
+      const DF2 cu2 = df2_mul_ny(cu, cu, ncu);
+      const DF2 E1 = df2_add_fast(df2_mul_ny(cu2, C24, nC24), A2v);
+      const DF2 E = df2_add_fast(df2_mul_ny(E1, cu2, df2_neg_hi(cu2)), A0v);
+      const DF2 O = df2_mul_ny(df2_add_fast(df2_mul_ny(cu2, C6, nC6), A1v), cu, ncu);
+      const DF2 sE = df2_mul_nx(scv, E, nsc), sO = df2_mul_nx(scv, O, nsc);
+      const DF2 fp = df2_add_fast(sE, sO), fm = df2_sub_fast(sE, sO);  // sc (E + O), sc (E - O)
+      const int lp = 4 * g + 1;  // populations 4g+1, 4g+2 (pair 2g) and 4g+3, 4g+4 (pair 2g+1)
+      dst[sidx(a, lp, y, x)] = fma(a.omc, s_f[lp][tid], df_to_double_bits(df2_lane0(fp)));
+      dst[sidx(a, lp + 1, y, x)] = fma(a.omc, s_f[lp + 1][tid], df_to_double_bits(df2_lane0(fm)));
+      dst[sidx(a, lp + 2, y, x)] = fma(a.omc, s_f[lp + 2][tid], df_to_double_bits(df2_lane1(fp)));
+      dst[sidx(a, lp + 3, y, x)] = fma(a.omc, s_f[lp + 3][tid], df_to_double_bits(df2_lane1(fm)));
     }
   }
 }

@@ -44,9 +44,10 @@ struct Codec<LBM_FP32_SHIFTED> {
 
 // The regularised collide is latency-bound on its fixed-point sums: capping
 // it at 96 registers (5 blocks per SM, some spills) measured 27% faster than
-// the unconstrained 163 registers (3 blocks).
+// the unconstrained 163 registers (3 blocks).  The double-float collide gains
+// 2-3% from the same cap (60 bytes of spill, 4 -> 5 blocks per SM).
 template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false>
-__global__ void __launch_bounds__(BX * BY, REG ? 5 : 0) step_kernel(const void* __restrict__ src_,
+__global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a) {
   using T = typename Codec<PREC>::T;
   const int x = blockIdx.x * BX + threadIdx.x;
