@@ -324,7 +324,7 @@ def rollout_study(steps, torch):
 
 def batch_study(steps, torch, lattices=64, tile=-1):
     """64 independent RT lattices of uneven sizes and parameters, FP32-store,
-    autotuned tile, `steps` steps as one CUDA-graph launch."""
+    autotuned launch candidate, `steps` steps as one CUDA-graph launch."""
     import synth
     from paper_1703_00186_gb300.batch import Batch
     specs = synth.batch_lattices(lattices, 7)
@@ -370,10 +370,11 @@ def batch_study(steps, torch, lattices=64, tile=-1):
     ms_p = e0.elapsed_time(e1)
     status_p = b.status()
     shapes = Batch.tile_shapes()
+    labels = Batch.tile_labels()
     return {"lattices": len(b), "sites": b.sites, "steps": steps, "graph_launches": 1,
-            "kernel_launches": steps, "ms": ms, "mlups": b.sites * steps / (ms * 1e-3) / 1e6,
-            "tile": shapes[best],
-            "autotune_ms_per_step": {f"{bx}x{by}x{rows}": t for (bx, by, rows), t in zip(shapes, times)},
+            "kernel_launches": steps * (len(b) if labels[best].startswith("per-lattice") else 1), "ms": ms, "mlups": b.sites * steps / (ms * 1e-3) / 1e6,
+            "tile": shapes[best], "launch": labels[best],
+            "autotune_ms_per_step": dict(zip(labels, times)),
             "persistent": {"ms": ms_p, "mlups": b.sites * steps / (ms_p * 1e-3) / 1e6, "status": status_p,
                            "what": "one cooperative launch, grid barrier between steps, 32x4 blocks x 8 rows"},
             "lattices_finite_after": finite,

@@ -2,20 +2,28 @@
  * lbm_batch.h - many independent D2Q37 lattices stepped together.
  *
  * A batch holds lattices of uneven sizes and parameters (each with its own
- * walls, tau, g and FP32 shift) that share one precision.  One time step of
- * the whole batch is one kernel launch whose blocks walk a single work list
- * of tiles spanning every lattice (each tile runs the fused propagate, bc and
- * collide of Sect. 2 / eq. 1 on its lattice); n steps are captured once into
- * a CUDA graph and replayed with one graph launch.  The tile shape is chosen
- * by lbm_batch_autotune, which times every candidate shape on the batch
- * itself.  The paper has no batched mode; the per-lattice step is the one of
- * include/lbm.h (same readings, layout and population order).
+ * walls, tau, g and FP32 shift) that share one precision.  n steps of the
+ * whole batch are captured once into a CUDA graph and replayed with one graph
+ * launch.  Two ways to launch a step are candidates:
+ *  - one kernel launch whose blocks walk a single work list of tiles spanning
+ *    every lattice (each tile runs the fused propagate, bc and collide of
+ *    Sect. 2 / eq. 1 on its lattice, with that lattice's constants staged in
+ *    shared memory); nine tile shapes;
+ *  - one launch of the single-lattice step kernel per lattice (its constants
+ *    in the kernel parameters), the lattices spread over eight streams that
+ *    the graph runs concurrently, each lattice's steps in order.
+ * lbm_batch_autotune times every candidate on the batch itself and keeps the
+ * fastest.  The paper has no batched mode; the per-lattice step is the one of
+ * include/lbm.h (same readings, layout and population order).  The
+ * candidates agree to rounding: each is its own compiled kernel, and float
+ * multiply-add contraction may differ between them.
  *
  * OWNERSHIP.  The caller owns every lattice buffer (two per lattice, in the
  * state layout of include/lbm.h) and the stream.  The batch allocates its
  * own device tables (lattice parameters, tile offsets, and for every tile
  * shape the lattice of each tile: 4 bytes per tile, about 1 MB per shape for
- * 33 M sites) and its CUDA graphs; lbm_batch_destroy releases them.
+ * 33 M sites), eight streams for the per-lattice launches, and its CUDA
+ * graphs; lbm_batch_destroy releases them.
  *
  * ERRORS.  As in include/lbm.h: LBM_OK or a negative LBM_ERR_* code, with a
  * message from lbm_batch_last_error().
@@ -42,12 +50,16 @@ typedef struct lbm_lattice_desc {
 
 typedef struct lbm_batch lbm_batch;
 
-/* Number of tile shapes lbm_batch_autotune chooses from, the block shape of
- * candidate `i` (threads along x and y) and its sites per thread along y
- * (a tile covers bx x (by * rows) sites; LBM_ERR_INVALID for a bad i). */
+/* Number of launch candidates lbm_batch_autotune chooses from (the nine tile
+ * shapes of the one-launch batch kernel, then the per-lattice launches), the
+ * block shape of candidate `i` (threads along x and y), its sites per thread
+ * along y (a tile covers bx x (by * rows) sites), and whether it launches
+ * the single-lattice kernel once per lattice (1) or is a tile shape (0).
+ * LBM_ERR_INVALID for a bad i. */
 int lbm_batch_tile_count(void);
 int lbm_batch_tile_shape(int i, int* bx, int* by);
 int lbm_batch_tile_rows(int i);
+int lbm_batch_tile_per_lattice(int i);
 
 /* Create a batch of n >= 1 lattices in `precision` (LBM_FP64 or
  * LBM_FP32_SHIFTED).  descs is a host array of n entries.  stream: cudaStream_t. */
@@ -60,12 +72,13 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy,
                    const double* T);
 
-/* Select tile shape `tile` (0 .. lbm_batch_tile_count()-1). */
+/* Select launch candidate `tile` (0 .. lbm_batch_tile_count()-1). */
 int lbm_batch_set_tile(lbm_batch* b, int tile);
 
-/* Time every tile shape over `steps` batch steps each (after one untimed
- * step), keep the fastest and return its index in *best (and, if times_ms is
- * not NULL, each candidate's time per step in times_ms[]).  The lattices
+/* Time every launch candidate over `steps` batch steps each (after one
+ * untimed step), keep the fastest and return its index in *best (and, if
+ * times_ms is not NULL, each candidate's time per step in
+ * times_ms[lbm_batch_tile_count()]).  The lattices
  * advance by (steps + 1) x lbm_batch_tile_count() steps: re-initialise
  * afterwards.  Synchronises the stream. */
 int lbm_batch_autotune(lbm_batch* b, int steps, int* best, double* times_ms);

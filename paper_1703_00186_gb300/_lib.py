@@ -77,6 +77,7 @@ SIGNATURES = {
     "lbm_constants": (c_int, [c_void_p, P(c_double), P(c_double), P(c_double), P(c_double)]),
     "lbm_probe_fma": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
     "lbm_batch_tile_count": (c_int, []),
+    "lbm_batch_tile_per_lattice": (c_int, [c_int]),
     "lbm_batch_tile_shape": (c_int, [c_int, P(c_int), P(c_int)]),
     "lbm_batch_tile_rows": (c_int, [c_int]),
     "lbm_batch_create": (c_int, [P(c_void_p), c_int, P(LbmLatticeDesc), c_int, c_void_p]),

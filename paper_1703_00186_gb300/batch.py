@@ -77,7 +77,8 @@ class Batch:
     @staticmethod
     def tile_shapes():
         """(threads along x, threads along y, sites per thread along y) of every
-        tile shape the autotuner chooses from."""
+        launch candidate the autotuner chooses from: the tile shapes of the
+        one-launch batch kernel, then the per-lattice launches."""
         lib = L.load()
         out = []
         for i in range(lib.lbm_batch_tile_count()):
@@ -85,6 +86,14 @@ class Batch:
             lib.lbm_batch_tile_shape(i, ctypes.byref(bx), ctypes.byref(by))
             out.append((bx.value, by.value, lib.lbm_batch_tile_rows(i)))
         return out
+
+    @staticmethod
+    def tile_labels():
+        """A name for every launch candidate ("32x4x8" for a tile shape,
+        "per-lattice 32x4" for the per-lattice launches)."""
+        lib = L.load()
+        return [f"per-lattice {bx}x{by}" if lib.lbm_batch_tile_per_lattice(i) == 1 else f"{bx}x{by}x{rows}"
+                for i, (bx, by, rows) in enumerate(Batch.tile_shapes())]
 
     def set_tile(self, t: int):
         self._check(self.lib.lbm_batch_set_tile(self.h, int(t)))

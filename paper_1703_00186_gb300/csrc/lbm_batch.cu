@@ -23,6 +23,7 @@
 namespace lbm {
 
 int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t errlen);
+cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a, cudaStream_t s);
 size_t element_size(int precision);
 int storage_prec(int precision);
 cudaError_t launch_init(int prec, void* dst, const double* rho, const double* ux, const double* uy,
@@ -43,6 +44,12 @@ constexpr int kTileBY[kTiles] = {4, 8, 2, 1, 2, 4, 4, 4, 4};
 // sites per thread along y: a tile covers kTileBY * kTileRows rows, so the
 // per-tile work (lattice lookup, constants, barriers) is shared by more sites
 constexpr int kTileRows[kTiles] = {1, 1, 1, 1, 1, 1, 2, 4, 8};
+// Launch candidate kTiles is not a tile shape: every lattice is stepped by the
+// single-lattice kernel (its constants in the kernel parameters, 32 x 4
+// blocks), the lattices spread over kAux streams, all captured in one graph.
+constexpr int kPerLattice = kTiles;
+constexpr int kCandidates = kTiles + 1;
+constexpr int kAux = 8;
 
 template <int PREC>
 struct BCodec;
@@ -252,6 +259,9 @@ struct lbm_batch {
   int parity;
   long long sites;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (n, parity, tile)
+  cudaStream_t aux[kAux];  // per-lattice launches: the lattices' streams
+  std::vector<int> order;  // lattices by decreasing size
+  std::vector<int> lane;   // stream of each lattice (balanced by sites)
   GridBarrier* d_bar;  // persistent-kernel barrier state
   char err[512];
 };
@@ -292,7 +302,46 @@ void free_batch(lbm_batch* b) {
   if (b->d_ent) cudaFree(b->d_ent);
   if (b->d_bar) cudaFree(b->d_bar);
   if (b->capture) cudaStreamDestroy(b->capture);
+  for (int k = 0; k < kAux; ++k)
+    if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
   delete b;
+}
+
+// Capture n steps of every lattice, one single-lattice kernel launch per
+// lattice and step, on the lattices' streams (forked from and joined back to
+// the capture stream).  A lattice's steps stay in order on its stream; the
+// lattices run concurrently.
+cudaError_t capture_per_lattice(lbm_batch* b, int n) {
+  cudaEvent_t fork = nullptr, join[kAux] = {};
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int k = 0; k < kAux && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, b->capture);
+  bool forked[kAux] = {};
+  for (int k = 0; k < kAux && e == cudaSuccess; ++k) {
+    e = cudaStreamWaitEvent(b->aux[k], fork, 0);
+    forked[k] = e == cudaSuccess;
+  }
+  for (size_t j = 0; j < b->order.size() && e == cudaSuccess; ++j) {
+    const int i = b->order[j];
+    int p = b->parity;
+    for (int t = 0; t < n && e == cudaSuccess; ++t) {
+      e = launch_step(b->precision, true, p ? b->fb[i] : b->fa[i], p ? b->fa[i] : b->fb[i], b->args[i],
+                      b->aux[b->lane[i]]);
+      p ^= 1;
+    }
+  }
+  // join every stream that was forked, also after an error, so the capture
+  // can end
+  for (int k = 0; k < kAux; ++k) {
+    if (!forked[k]) continue;
+    const cudaError_t r = cudaEventRecord(join[k], b->aux[k]);
+    const cudaError_t w = r == cudaSuccess ? cudaStreamWaitEvent(b->capture, join[k], 0) : r;
+    if (e == cudaSuccess) e = w;
+  }
+  for (int k = 0; k < kAux; ++k)
+    if (join[k]) cudaEventDestroy(join[k]);
+  if (fork) cudaEventDestroy(fork);
+  return e;
 }
 
 // Graph of n batch steps starting at parity p with the current tile shape.
@@ -307,10 +356,14 @@ int get_graph(lbm_batch* b, int n, cudaGraphExec_t* out) {
   int rc = bcuda(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "graph capture");
   if (rc) return rc;
   cudaError_t le = cudaSuccess;
-  int p = b->parity;
-  for (int i = 0; i < n && le == cudaSuccess; ++i) {
-    le = launch_batch(b, p, b->capture);
-    p ^= 1;
+  if (b->tile == kPerLattice) {
+    le = capture_per_lattice(b, n);
+  } else {
+    int p = b->parity;
+    for (int i = 0; i < n && le == cudaSuccess; ++i) {
+      le = launch_batch(b, p, b->capture);
+      p ^= 1;
+    }
   }
   cudaError_t ee = cudaStreamEndCapture(b->capture, &g);
   if (le != cudaSuccess) {
@@ -332,16 +385,24 @@ int get_graph(lbm_batch* b, int n, cudaGraphExec_t* out) {
 
 extern "C" {
 
-int lbm_batch_tile_count(void) { return kTiles; }
+int lbm_batch_tile_count(void) { return kCandidates; }
 
 int lbm_batch_tile_shape(int i, int* bx, int* by) {
-  if (i < 0 || i >= kTiles || !bx || !by) return LBM_ERR_INVALID;
-  *bx = kTileBX[i];
-  *by = kTileBY[i];
+  if (i < 0 || i >= kCandidates || !bx || !by) return LBM_ERR_INVALID;
+  *bx = i == kPerLattice ? 32 : kTileBX[i];  // the single-lattice kernel's 32 x 4 blocks
+  *by = i == kPerLattice ? 4 : kTileBY[i];
   return LBM_OK;
 }
 
-int lbm_batch_tile_rows(int i) { return i < 0 || i >= kTiles ? LBM_ERR_INVALID : kTileRows[i]; }
+int lbm_batch_tile_rows(int i) {
+  if (i < 0 || i >= kCandidates) return LBM_ERR_INVALID;
+  return i == kPerLattice ? 1 : kTileRows[i];
+}
+
+int lbm_batch_tile_per_lattice(int i) {
+  if (i < 0 || i >= kCandidates) return LBM_ERR_INVALID;
+  return i == kPerLattice ? 1 : 0;
+}
 
 int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int precision, void* stream) {
   if (!out) return LBM_ERR_INVALID;
@@ -418,6 +479,31 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
     free_batch(b);
     return LBM_ERR_CUDA;
   }
+  for (int k = 0; k < kAux; ++k) {
+    if (cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return LBM_ERR_CUDA;
+    }
+  }
+  // per-lattice launches: largest lattices first, each to the stream with the
+  // fewest sites so far
+  b->order.resize(n);
+  b->lane.assign(n, 0);
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) {
+    return (long long)b->args[p].lx * b->args[p].ly > (long long)b->args[q].lx * b->args[q].ly;
+  });
+  {
+    long long load[kAux] = {};
+    for (int i : b->order) {
+      int k = 0;
+      for (int m = 1; m < kAux; ++m)
+        if (load[m] < load[k]) k = m;
+      b->lane[i] = k;
+      load[k] += (long long)b->args[i].lx * b->args[i].ly;
+    }
+  }
   b->tile = 0;
   b->parity = 0;
   *out = b;
@@ -441,7 +527,7 @@ int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, con
 
 int lbm_batch_set_tile(lbm_batch* b, int tile) {
   if (!b) return LBM_ERR_INVALID;
-  if (tile < 0 || tile >= kTiles) return bfail(b, LBM_ERR_INVALID, "tile %d out of range", tile);
+  if (tile < 0 || tile >= kCandidates) return bfail(b, LBM_ERR_INVALID, "tile %d out of range", tile);
   b->tile = tile;
   return LBM_OK;
 }
@@ -472,7 +558,7 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* best, double* times_ms) {
   }
   double best_t = 1e300;
   int best_i = 0;
-  for (int t = 0; t < kTiles && rc == LBM_OK; ++t) {
+  for (int t = 0; t < kCandidates && rc == LBM_OK; ++t) {
     b->tile = t;
     rc = lbm_batch_step(b, 1);  // warm-up (and graph capture of the 1-step graph)
     cudaGraphExec_t exec;

@@ -58,11 +58,13 @@ def oracle_run(spec, f, n):
 
 def test_tile_shapes():
     shapes = Batch.tile_shapes()
-    assert len(shapes) == 9
+    assert len(shapes) == 10
     assert all(bx * by <= 256 and rows >= 1 for bx, by, rows in shapes)
+    labels = Batch.tile_labels()
+    assert labels[-1] == "per-lattice 32x4" and not any(lb.startswith("per") for lb in labels[:-1])
 
 
-@pytest.mark.parametrize("tile", range(9))
+@pytest.mark.parametrize("tile", range(10))
 def test_batch_fp64_matches_oracle_for_every_tile_shape(tile):
     specs, flds = build("fp64")
     b = Batch(specs, precision="fp64")
@@ -77,9 +79,11 @@ def test_batch_fp64_matches_oracle_for_every_tile_shape(tile):
     assert b.status() == 0
 
 
-def test_batch_fp32_one_step_matches_oracle():
+@pytest.mark.parametrize("tile", [0, 9])
+def test_batch_fp32_one_step_matches_oracle(tile):
     specs, flds = build("fp32")
     b = Batch(specs, precision="fp32")
+    b.set_tile(tile)
     for i, f in enumerate(flds):
         b.init(i, *f)
     b.step(1)
@@ -151,7 +155,7 @@ def test_bounded_barrier_wait_times_out_and_batch_stays_usable():
         assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, flds[i], 3)) <= 1e-12
 
 
-@pytest.mark.parametrize("tile", [0, 8])
+@pytest.mark.parametrize("tile", [0, 8, 9])
 def test_batch_fp64df_matches_oracle(tile):
     # float64 storage with the double-float collide, graph and persistent launches
     specs, flds = build("fp64df")
@@ -163,3 +167,28 @@ def test_batch_fp64df_matches_oracle(tile):
     assert b.status() == 0
     for i, (s, f) in enumerate(zip(specs, flds)):
         assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, f, 4)) <= 1e-12, i
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp64df", 1e-13)])
+def test_per_lattice_launches_match_the_batch_kernel(precision, tol):
+    # candidate 9 steps each lattice with the single-lattice kernel on one of
+    # eight streams: the batch kernel's arithmetic, compiled in another kernel
+    # (float multiply-add contraction may differ), so the states agree to
+    # rounding (odd and even step counts, two cached graphs)
+    specs, flds = build(precision)
+    a = Batch(specs, precision=precision)
+    b = Batch(specs, precision=precision)
+    a.set_tile(8)
+    b.set_tile(9)
+    for i, f in enumerate(flds):
+        a.init(i, *f)
+        b.init(i, *f)
+    a.step(3).step(2)
+    b.step(3).step(2)
+    assert a.status() == 0 and b.status() == 0
+    for i in range(len(specs)):
+        sa, sb = a.state(i).cpu().numpy().astype(np.float64), b.state(i).cpu().numpy().astype(np.float64)
+        if precision == "fp32":
+            w = K["w"][:, None, None] * specs[i]["rho0"]
+            sa, sb = sa + w, sb + w
+        assert plane_err(sb, sa) <= tol, i
