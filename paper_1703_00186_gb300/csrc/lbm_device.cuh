@@ -357,29 +357,38 @@ __device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
   const float2 C1 = f2s(3072.0f), C1n = f2s(-3072.0f), C2 = f2s(0x1.8p-11f);
   const Split s0 = split2(d[0]);
   float2 r2 = f2(s0.h, 0.f), e2 = f2(0.f, 0.f), jx2 = f2(0.f, 0.f), jy2 = f2(0.f, 0.f);
-  unsigned rm = s0.bits, em = 0u, jxm = 0u, jym = 0u, e_off = 0u;
+  // integer parts (modulo 2^32, exact): m+ + m- summed per shell, and
+  // +-(m+ - m-) per |xi_x| and |xi_y| value; the weights are applied once
+  unsigned sh[NSHELL] = {}, ax_sum[4] = {}, ay_sum[4] = {};
+  unsigned e_off = 0u;
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
     const float2 v = f2(d[2 * k + 1], d[2 * k + 2]);
     const float2 h = add2(add2(v, C1), C1n);  // both lanes of split2
     const float2 t = add2(sub2(v, h), C2);
     const unsigned pb = __float_as_uint(t.x), qb = __float_as_uint(t.y);
-    const unsigned sm = pb + qb, dm = pb - qb;
     const int ax = rep_x(k), ay = rep_y(k), c2 = ax * ax + ay * ay;
     r2 = add2(r2, h);
-    rm += sm;
     e2 = c2 == 1 ? add2(e2, h) : fma2(f2s((float)c2), h, e2);
-    em += (unsigned)c2 * sm;
+    sh[pair_shell(k)] += pb + qb;
     e_off += 2u * (unsigned)c2;
     if (ax != 0) {
       jx2 = fma2(f2((float)ax, (float)-ax), h, jx2);
-      jxm += (unsigned)ax * dm;
+      ax_sum[ax > 0 ? ax : -ax] += ax > 0 ? pb - qb : qb - pb;
     }
     if (ay != 0) {
       jy2 = fma2(f2((float)ay, (float)-ay), h, jy2);
-      jym += (unsigned)ay * dm;
+      ay_sum[ay > 0 ? ay : -ay] += ay > 0 ? pb - qb : qb - pb;
     }
   }
+  unsigned rm = s0.bits, em = 0u;
+#pragma unroll
+  for (int j = 1; j < NSHELL; ++j) {
+    rm += sh[j];
+    em += (unsigned)shell_sq(j) * sh[j];
+  }
+  const unsigned jxm = ax_sum[1] + 2u * ax_sum[2] + 3u * ax_sum[3];
+  const unsigned jym = ay_sum[1] + 2u * ay_sum[2] + 3u * ay_sum[3];
   const SplitAcc r{r2.x + r2.y, rm - (unsigned)NPOP * K2}, e{e2.x + e2.y, em - e_off * K2};
   const SplitAcc jx{jx2.x + jx2.y, jxm}, jy{jy2.x + jy2.y, jym};
   return {split_result(r), split_result(jx), split_result(jy), split_result(e)};
