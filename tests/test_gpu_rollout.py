@@ -3,7 +3,8 @@
 * the gradient equals the oracle's discrete-adjoint gradient (float64 both
   sides; <= 1e-10 relative, the sweep accumulates rounding over the steps);
 * it matches float64 central finite differences of the GPU forward rollout
-  on 16 seeded directions to <= 1e-6 relative (the BASELINE tolerance);
+  on 16 seeded directions to <= 1e-6 relative (the tolerance set for the
+  adjoint);
 * checkpoint spacing K does not change the result beyond rounding.
 """
 import numpy as np
