@@ -48,6 +48,8 @@ const Quadrature* quadrature(char* err, size_t errlen) {
 }
 }  // namespace
 
+size_t element_size(int precision);
+
 // Fill the per-launch constants of a lattice.  Returns 0 or an error code
 // with a message in err.
 int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t errlen) {
@@ -84,9 +86,10 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->plane = (long long)(p.ly + 2 * HALO) * p.lx;
   a->idx32 = (long long)NPOP * a->plane < (1LL << 31) ? 1 : 0;
   if (a->idx32) {
+    const long long es = (long long)element_size(p.precision);
     for (int l = 0; l < NPOP; ++l) {
-      a->plane_off[l] = (int)(l * a->plane);
-      a->pull_off[l] = (int)(l * a->plane - (long long)vy(l) * p.lx - vx(l));
+      a->plane_off[l] = l * a->plane * es;
+      a->pull_off[l] = (l * a->plane - (long long)vy(l) * p.lx - vx(l)) * es;
     }
   }
   a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;

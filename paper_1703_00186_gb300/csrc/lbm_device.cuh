@@ -60,9 +60,9 @@ __device__ __forceinline__ bool fast_site(const LatticeArgs& a, int x) {
 template <typename T, bool COHERENT = false>
 __device__ __forceinline__ void pull_fast(const T* __restrict__ src, int site, const LatticeArgs& a,
                                           T (&f)[NPOP]) {
-  const T* s = src + site;
+  const char* s = reinterpret_cast<const char*>(src + site);
 #pragma unroll
-  for (int l = 0; l < NPOP; ++l) f[l] = load<COHERENT>(s + a.pull_off[l]);
+  for (int l = 0; l < NPOP; ++l) f[l] = load<COHERENT>(reinterpret_cast<const T*>(s + a.pull_off[l]));
 }
 
 // Store the 37 populations of a site (any site, fast indices if idx32).
@@ -70,9 +70,9 @@ template <typename T>
 __device__ __forceinline__ void store_site(T* __restrict__ dst, int x, int y, const LatticeArgs& a,
                                            const T (&f)[NPOP]) {
   if (a.idx32) {
-    T* d = dst + site_off(a, y, x);
+    char* d = reinterpret_cast<char*>(dst + site_off(a, y, x));
 #pragma unroll
-    for (int l = 0; l < NPOP; ++l) d[a.plane_off[l]] = f[l];
+    for (int l = 0; l < NPOP; ++l) *reinterpret_cast<T*>(d + a.plane_off[l]) = f[l];
   } else {
 #pragma unroll
     for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = f[l];
@@ -234,80 +234,22 @@ __device__ __forceinline__ Moments site_moments(Get get) {
   return mo;
 }
 
-// Double-float accumulation (Knuth's TwoSum and the FMA exact product): a
-// sum is kept as hi + lo, where every addition into hi is error-free and the
-// rounding errors are collected in lo.  For sums of float32 values with small
-// integer weights this bounds the error by about 2 u^2 sum |x| (u = 2^-24),
-// the size of the rounding error of a float64 summation.
-struct F2 {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void f2_add(F2& acc, float x) {
-  const float s = acc.hi + x;
-  const float bb = s - acc.hi;
-  const float e = (acc.hi - (s - bb)) + (x - bb);
-  acc.hi = s;
-  acc.lo += e;
-}
-
-// acc += k x for a small integer k (k x rounded, its error added exactly).
-__device__ __forceinline__ void f2_add_mul(F2& acc, int k, float x) {
-  if (k == 1) {
-    f2_add(acc, x);
-  } else if (k == -1) {
-    f2_add(acc, -x);
-  } else if (k == 2 || k == -2 || k == 4 || k == 8) {
-    f2_add(acc, (float)k * x);  // power-of-two multiples are exact
-  } else {
-    const float p = (float)k * x;
-    const float e = fmaf((float)k, x, -p);
-    f2_add(acc, p);
-    acc.lo += e;
-  }
-}
-
-__device__ __forceinline__ double f2_to_double(const F2& a) { return (double)a.hi + (double)a.lo; }
-
-// Moment sums of 37 float32 values (rho, Jx, Jy, Exi as in moment_sums),
-// accumulated in double-float.
+// Moment sums (rho, Jx, Jy, Exi as in moment_sums) in double-float.
 struct MomentsDF {
   DF rho, Jx, Jy, Exi;
 };
 
-__device__ __forceinline__ DF f2_norm(const F2& a) { return df_fast_two_sum(a.hi, a.lo); }
-
-__device__ __forceinline__ MomentsDF moment_sums_df(const float (&d)[NPOP]) {
-  F2 r{d[0], 0.f}, jx{0.f, 0.f}, jy{0.f, 0.f}, e{0.f, 0.f};
-  bool jx0 = true, jy0 = true, e0 = true;
-#pragma unroll
-  for (int l = 1; l < NPOP; ++l) {
-    f2_add(r, d[l]);
-    if (vx(l) != 0) {
-      if (jx0) { jx.hi = (float)vx(l) * d[l]; jx.lo = fmaf((float)vx(l), d[l], -jx.hi); jx0 = false; }
-      else f2_add_mul(jx, vx(l), d[l]);
-    }
-    if (vy(l) != 0) {
-      if (jy0) { jy.hi = (float)vy(l) * d[l]; jy.lo = fmaf((float)vy(l), d[l], -jy.hi); jy0 = false; }
-      else f2_add_mul(jy, vy(l), d[l]);
-    }
-    if (e0) { e.hi = (float)sq(l) * d[l]; e.lo = fmaf((float)sq(l), d[l], -e.hi); e0 = false; }
-    else f2_add_mul(e, sq(l), d[l]);
-  }
-  return {f2_norm(r), f2_norm(jx), f2_norm(jy), f2_norm(e)};
-}
-
-// Moment sums of 37 float32 values by an exact three-level split of every
-// value d = h + m + l (the "magic number" rounding of Dekker and Knuth:
-// adding and subtracting 1.5 * 2^k rounds to a multiple of 2^(k-23)):
+// Moment sums of 37 float32 values by a split of every value d = h + m + e
+// (the "magic number" rounding of Dekker and Knuth: adding and subtracting
+// 1.5 * 2^k rounds to a multiple of 2^(k-23)):
 //   h: d rounded to a multiple of 2^-12; for |d| < 4 every weighted sum of
 //      the h (integer weights <= 10, 37 terms) stays below 2^23 grid steps,
 //      so it is exact in float32;
 //   m: the rest rounded to a multiple of 2^-34, read off as an integer
 //      (|m| 2^34 <= 2^21) and summed exactly in int32;
-//   l: the remainder, |l| <= 2^-35, summed in float32 (error < 2^-50).
-// The result is returned as double-float.  Values with |d| >= 4 (a diverged
-// lattice) are still summed, only no longer exactly.
+//   e: the remainder, |e| <= 2^-35, dropped.
+// Values with |d| >= 4 (a diverged lattice) are still summed, only no longer
+// exactly.
 struct SplitAcc {
   float h;
   unsigned m;  // integer part, accumulated modulo 2^32 (the true sum fits in int32)
@@ -352,7 +294,12 @@ __device__ __forceinline__ Split split2(float v) {
 // as one partial sum per lane (every partial sum is exact, so is their total);
 // the integer parts combine the pair first: the even moments take m+ + m-,
 // the odd ones m+ - m-.
-__device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
+// The four sums (rho, Jx, Jy, Exi) before the conversion to double-float.
+struct SplitSums {
+  SplitAcc r, jx, jy, e;
+};
+
+__device__ __forceinline__ SplitSums moment_sums_split(const float (&d)[NPOP]) {
   constexpr unsigned K2 = 0x3a400000u;  // bit pattern of 1.5 * 2^-11
   const float2 C1 = f2s(3072.0f), C1n = f2s(-3072.0f), C2 = f2s(0x1.8p-11f);
   const Split s0 = split2(d[0]);
@@ -391,7 +338,22 @@ __device__ __forceinline__ MomentsDF moment_sums_split(const float (&d)[NPOP]) {
   const unsigned jym = ay_sum[1] + 2u * ay_sum[2] + 3u * ay_sum[3];
   const SplitAcc r{r2.x + r2.y, rm - (unsigned)NPOP * K2}, e{e2.x + e2.y, em - e_off * K2};
   const SplitAcc jx{jx2.x + jx2.y, jxm}, jy{jy2.x + jy2.y, jym};
-  return {split_result(r), split_result(jx), split_result(jy), split_result(e)};
+  return {r, jx, jy, e};
+}
+
+__device__ __forceinline__ MomentsDF split_moments(const SplitSums& s) {
+  return {split_result(s.r), split_result(s.jx), split_result(s.jy), split_result(s.e)};
+}
+
+// b - a for two split sums of the same kind, rounded once to float32: the h
+// parts are on the 2^-12 grid and below 2^11, so h_b - h_a is exact; the
+// integer difference (modulo 2^32; the true difference fits in int32) is
+// split into two pieces that convert exactly, and only the last addition
+// rounds.
+__device__ __forceinline__ float split_diff(const SplitAcc& b, const SplitAcc& a) {
+  const int dm = (int)(b.m - a.m);
+  const float dh = b.h - a.h;
+  return fmaf((float)(dm & 0xfff), 0x1p-34f, fmaf((float)(dm >> 12), 0x1p-22f, dh));
 }
 
 // Site state derived from the moments: velocity in xi units and temperature.
@@ -479,15 +441,17 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 template <bool PAIRED = true>
 __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
   MomentsDF dev;
+  SplitSums dev_raw;
   float rf = 0.f;
   // Both passes share one copy of the moment-sum code (a rolled loop of two
   // iterations): the kernel is instruction-issue bound and a smaller body
   // keeps it in the instruction cache.
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
-    const MomentsDF m = moment_sums_split(d);
+    const SplitSums m = moment_sums_split(d);
     if (pass == 0) {
-      dev = m;
+      dev_raw = m;
+      dev = split_moments(m);
       const DF rho = df_add(dev.rho, dfc(a.df_rho0));
       const DF inv = df_rcp(rho);
       const float invf = inv.hi;
@@ -542,16 +506,14 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
       // the equilibrium shift (omega tau = 1), deviation form, xi units,
       // g_xi = g / r: mass and Jx unchanged, Jy - rho g_xi,
       // Exi - 2 g_xi Jy + rho g_xi^2 (the gravity terms are ~1e-5 of the
-      // sums, float32 is enough for them).
-      const MomentsDF& nw = m;
+      // sums, float32 is enough for them).  The defects (~1e-8 of the sums)
+      // are the differences of the two passes' sums less the target change,
+      // each rounded once.
       const float gr = a.df_g_r[0];
-      const DF tjy = df_add(dev.Jy, -rf * gr);
-      const DF te = df_add(dev.Exi, fmaf(rf * gr, gr, -2.0f * gr * dev.Jy.hi));
-      // defects (~1e-8 of the sums): one rounding of the difference at most
-      const float dm = (nw.rho.hi - dev.rho.hi) + (nw.rho.lo - dev.rho.lo);
-      const float djx = (nw.Jx.hi - dev.Jx.hi) + (nw.Jx.lo - dev.Jx.lo);
-      const float djy = (nw.Jy.hi - tjy.hi) + (nw.Jy.lo - tjy.lo);
-      const float de = (nw.Exi.hi - te.hi) + (nw.Exi.lo - te.lo);
+      const float dm = split_diff(m.r, dev_raw.r);
+      const float djx = split_diff(m.jx, dev_raw.jx);
+      const float djy = fmaf(rf, gr, split_diff(m.jy, dev_raw.jy));
+      const float de = split_diff(m.e, dev_raw.e) - fmaf(rf * gr, gr, -2.0f * gr * dev.Jy.hi);
       d[0] += de - dm;
       d[1] += (-0.5f * de - djx) * 0.5f;  // xi = (1, 0)
       d[2] += (-0.5f * de + djx) * 0.5f;  // xi = (-1, 0)

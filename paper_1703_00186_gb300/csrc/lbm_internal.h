@@ -106,13 +106,16 @@ struct LatticeArgs {
   double ginv[63];        // inverse Gram blocks EE(36) OE(9) EO(9) OO(9)
   float df_c2_shell[NSHELL][2];
   unsigned int* status;  // device status word
-  // Site-relative element offsets for states of fewer than 2^31 elements
-  // (idx32 != 0): the pull source of population l of an interior column is
-  // site + pull_off[l], its destination site + plane_off[l].
+  // Site-relative offsets for states of fewer than 2^31 elements
+  // (idx32 != 0), in bytes of the lattice's storage type: the pull source of
+  // population l of an interior column lies pull_off[l] bytes from the site's
+  // element in plane 0, its destination plane_off[l] bytes from it.  Whole
+  // 64-bit byte offsets let every access add a kernel parameter to one
+  // per-thread pointer, with no per-access widening or scaling.
   int idx32;
-  int tma_loads;         // LBM_FLAG_TMA_LOADS
-  int pull_off[NPOP];    // l plane - xi_ly lx - xi_lx
-  int plane_off[NPOP];   // l plane
+  int tma_loads;              // LBM_FLAG_TMA_LOADS
+  long long pull_off[NPOP];   // (l plane - xi_ly lx - xi_lx) * element size
+  long long plane_off[NPOP];  // l plane * element size
 };
 
 }  // namespace lbm
