@@ -48,9 +48,9 @@ FP64_FLOP_PER_SITE = 547
 FP64_FLOP_PER_SITE_MOMENT_SUMS = 110
 FP64_INSTR_PER_SITE_NCU = 268
 # DRAM bytes per site of the float64 step (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one 2048 x 1024 launch, 1190.20 MB / 2097152 sites;
+# dram__bytes_write.sum of one 2048 x 1024 launch, 1190.50 MB / 2097152 sites;
 # traffic grows with the site count, so a full launch is scaled by sites).
-FP64_TRAFFIC_BYTES_PER_SITE_NCU = 567.53
+FP64_TRAFFIC_BYTES_PER_SITE_NCU = 567.67
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
