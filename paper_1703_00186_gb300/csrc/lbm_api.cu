@@ -108,6 +108,10 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   for (int j = 0; j < NSHELL; ++j) {
     a->w_shell[j] = q->w_shell[j];
     a->c2_shell[j] = q->c2_shell[j];
+    a->c2h_shell[j] = 0.5 * q->c2_shell[j];
+    a->c2q_shell[j] = 0.25 * q->c2_shell[j];
+    a->c4e_shell[j] = 0.125 * (q->c2_shell[j] * q->c2_shell[j]);
+    a->w6_shell[j] = q->w_shell[j] / 6.0;
   }
   if (a->regularized && regularization_gram_inverse(*q, a->ginv) != 0) {
     std::snprintf(err, errlen, "singular Gram matrix");

@@ -381,20 +381,26 @@ __device__ __forceinline__ SiteFields collide_fp64(double (&f)[NPOP], const Latt
   const double v_x = a.r2 * sf.ux, v_y = a.r2 * uys;
   const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
   const EqCoef B = eq_coef(U2, theta);
+  const double th2 = theta * theta;
   const double wr = a.omega * sf.rho;
   f[0] = fma(a.omc, f[0], (wr * a.w_shell[0]) * B.B00);
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
+    // A0 = B00 + B01 c2 + B02 c2^2, A1 = B10 + B11 c2, A2 = B20 + B21 c2 with
+    // B02 = theta^2 / 8, B11 = theta / 2, B21 = theta / 4 folded into the
+    // shell constants; the odd part carries the shell weight in its Horner
+    // coefficients, sO = cu (sc A1 + (sc / 6) cu^2), sc = omega rho w.
     const int j = pair_shell(k);
-    const double c2 = a.c2_shell[j];
-    const double A0 = fma(c2, fma(c2, B.B02, B.B01), B.B00);
-    const double A1 = fma(B.B11, c2, B.B10);
-    const double A2 = fma(B.B21, c2, B.B20);
+    const double A0 = fma(a.c4e_shell[j], th2, fma(a.c2_shell[j], B.B01, B.B00));
+    const double A1 = fma(theta, a.c2h_shell[j], B.B10);
+    const double A2 = fma(theta, a.c2q_shell[j], B.B20);
     const double sc = wr * a.w_shell[j];
+    const double sc6 = wr * a.w6_shell[j];
+    const double scA1 = sc * A1;
     const double cu = pair_cu<double>(k, v_x, v_y);
     const double cu2 = cu * cu;
     const double E = fma(cu2, fma(cu2, 1.0 / 24.0, A2), A0);
-    const double sO = sc * (cu * fma(cu2, 1.0 / 6.0, A1));
+    const double sO = cu * fma(cu2, sc6, scA1);
     f[2 * k + 1] = fma(a.omc, f[2 * k + 1], fma(sc, E, sO));    // sc (E + O)
     f[2 * k + 2] = fma(a.omc, f[2 * k + 2], fma(sc, E, -sO));   // sc (E - O)
   }

@@ -83,6 +83,11 @@ struct LatticeArgs {
   double rho0;           // FP32 shift density
   double w_shell[NSHELL];
   double c2_shell[NSHELL];
+  // per-shell multiples for the float64 collide: c2 / 2, c2 / 4, c2^2 / 8, w / 6
+  double c2h_shell[NSHELL];
+  double c2q_shell[NSHELL];
+  double c4e_shell[NSHELL];
+  double w6_shell[NSHELL];
   double q_bot[NPOP];
   double q_top[NPOP];
   float w_rho0_f[NPOP];  // w_l rho0 as float (FP32 decode of bc inputs)

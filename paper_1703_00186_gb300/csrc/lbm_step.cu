@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel
 // right edge with zeros.  The sums are exact in fixed point on the integer
 // pipe (float64 shuffles and adds only if a value is outside the fixed-point
 // range) and go to the row totals with one atomic add per quantity.
-__global__ void __launch_bounds__(BX * BY) step_observe_kernel(const double* __restrict__ src,
+__global__ void __launch_bounds__(BX * BY, 4) step_observe_kernel(const double* __restrict__ src,
                                                                double* __restrict__ dst, LatticeArgs a,
                                                                double* __restrict__ obs) {
   static_assert(BX == 32, "one warp per row segment");
