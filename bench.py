@@ -41,16 +41,16 @@ WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-
 # Algorithmic float64 work of the fused step per site, counted from the
 # collide's formulation (an FMA counts 2 flops), and the FP64 instructions per
 # site that ncu measured for the current kernel (profiles/step_kernel_fp64_*).
-# 110 of the 547 flops are the moment sums, which the kernel forms exactly in
+# 110 of the 540 flops are the moment sums, which the kernel forms exactly in
 # fixed point on the integer pipe (one rounding per sum) instead of with FP64
 # additions.
-FP64_FLOP_PER_SITE = 547
+FP64_FLOP_PER_SITE = 540
 FP64_FLOP_PER_SITE_MOMENT_SUMS = 110
-FP64_INSTR_PER_SITE_NCU = 268
+FP64_INSTR_PER_SITE_NCU = 261
 # DRAM bytes per site of the float64 step (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one 2048 x 1024 launch, 1190.50 MB / 2097152 sites;
+# dram__bytes_write.sum of one 2048 x 1024 launch, 1190.35 MB / 2097152 sites;
 # traffic grows with the site count, so a full launch is scaled by sites).
-FP64_TRAFFIC_BYTES_PER_SITE_NCU = 567.67
+FP64_TRAFFIC_BYTES_PER_SITE_NCU = 567.60
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
