@@ -26,6 +26,25 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_tensor(t, name, dtype, shape, device):
+    """Reject a tensor the kernels cannot take: every state, cotangent and
+    field pointer handed to liblbm.so (except the host-or-device checkpoint
+    copies) must be contiguous memory of the lattice's own GPU with the
+    expected dtype and shape.  A host pointer given to a kernel would be
+    dereferenced on the device, so this check runs before any call."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.device != device:
+        raise ValueError(f"{name}: tensor on {t.device}, the lattice lives on {device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    return t
+
+
 def _field(v, ly, lx, device):
     """A float64 (ly, lx) contiguous device tensor from a tensor or array."""
     if isinstance(v, torch.Tensor):
@@ -53,7 +72,10 @@ class Lattice:
         self.lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
-        self.device = torch.device(device if device is not None else "cuda")
+        dev = torch.device(device if device is not None else "cuda")
+        if dev.type != "cuda":
+            raise ValueError(f"device {dev} is not a CUDA device")
+        self.device = dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
         self.lx, self.ly = int(lx), int(ly)
         self.precision = precision
         prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED, "fp64df": L.LBM_FP64_DF}[precision]
@@ -96,6 +118,15 @@ class Lattice:
         except Exception:
             pass
 
+    def _state(self, t, name):
+        return _check_tensor(t, name, self.dtype, self.shape, self.device)
+
+    def _opt_state(self, t, name):
+        return None if t is None else self._state(t, name)
+
+    def _cotangent(self, t, name):
+        return _check_tensor(t, name, torch.float64, self.shape, self.device)
+
     def new_state(self, fill=float("nan")):
         return torch.full(self.shape, fill, dtype=self.dtype, device=self.device)
 
@@ -116,6 +147,8 @@ class Lattice:
 
     def step_from(self, src: torch.Tensor, dst: torch.Tensor):
         """One step from state src into state dst (context buffers untouched)."""
+        self._state(src, "src")
+        self._state(dst, "dst")
         self._check(self.lib.lbm_step_from(self.ctx, _ptr(src), _ptr(dst)))
         return dst
 
@@ -125,24 +158,35 @@ class Lattice:
         return self.buffers[0] if ptr == self.buffers[0].data_ptr() else self.buffers[1]
 
     def set_state(self, src: torch.Tensor):
+        """Copy a state (device memory, or host memory such as a pinned
+        tensor) into the current buffer, asynchronously on the lattice's
+        stream."""
         if src.dtype != self.dtype or tuple(src.shape) != self.shape:
             raise ValueError("state dtype/shape mismatch")
-        self._check(self.lib.lbm_set_state(self.ctx, _ptr(src.contiguous())))
+        if src.device.type == "cuda" and src.device != self.device:
+            raise ValueError(f"src: tensor on {src.device}, the lattice lives on {self.device}")
+        src = src.contiguous()
+        self._check(self.lib.lbm_set_state(self.ctx, _ptr(src)))
+        self._keep = src  # alive until the copy is ordered before later work
         return self
 
     def get_state(self, dst: torch.Tensor):
         if dst.dtype != self.dtype or tuple(dst.shape) != self.shape or not dst.is_contiguous():
             raise ValueError("state dtype/shape mismatch")
+        if dst.device.type == "cuda" and dst.device != self.device:
+            raise ValueError(f"dst: tensor on {dst.device}, the lattice lives on {self.device}")
         self._check(self.lib.lbm_get_state(self.ctx, _ptr(dst)))
         return dst
 
     def moments(self, f: torch.Tensor | None = None):
+        self._opt_state(f, "f")
         out = [torch.empty((self.ly, self.lx), dtype=torch.float64, device=self.device) for _ in range(4)]
         self._check(self.lib.lbm_moments(self.ctx, _ptr(f), *[_ptr(t) for t in out]))
         return tuple(out)
 
     def profiles(self, f: torch.Tensor | None = None) -> torch.Tensor:
         """Row averages (8, ly) of rho, u_x, u_y, T, T^2, u_y T, rho|u|^2/2, rho u_y."""
+        self._opt_state(f, "f")
         out = torch.empty((L.LBM_NOBS, self.ly), dtype=torch.float64, device=self.device)
         self._check(self.lib.lbm_profiles(self.ctx, _ptr(f), _ptr(out)))
         return out
@@ -155,20 +199,27 @@ class Lattice:
         return out[:rec.value]
 
     def propagate_bc(self, src: torch.Tensor, dst: torch.Tensor | None = None):
+        self._state(src, "src")
         if dst is None:
             dst = self.new_state()
+        self._state(dst, "dst")
         self._check(self.lib.lbm_propagate_bc(self.ctx, _ptr(src), _ptr(dst)))
         return dst
 
     def adjoint_step(self, f_t: torch.Tensor, lam_in: torch.Tensor, lam_out: torch.Tensor | None = None):
+        self._state(f_t, "f_t")
+        self._cotangent(lam_in, "lam_in")
         if lam_out is None:
             lam_out = self.new_cotangent()
+        self._cotangent(lam_out, "lam_out")
         self._check(self.lib.lbm_adjoint_step(self.ctx, _ptr(f_t), _ptr(lam_in), _ptr(lam_out)))
         return lam_out
 
     def moments_vjp(self, f, g_rho=None, g_ux=None, g_uy=None, g_T=None, lam_out=None):
+        self._state(f, "f")
         if lam_out is None:
             lam_out = self.new_cotangent()
+        self._cotangent(lam_out, "lam_out")
         gs = [None if g is None else _field(g, self.ly, self.lx, self.device) for g in (g_rho, g_ux, g_uy, g_T)]
         self._check(self.lib.lbm_moments_vjp(self.ctx, _ptr(f), *[_ptr(g) for g in gs], _ptr(lam_out)))
         self._keep = gs
@@ -176,12 +227,14 @@ class Lattice:
 
     def init_vjp(self, rho, ux, uy, T, lam):
         f = [_field(v, self.ly, self.lx, self.device) for v in (rho, ux, uy, T)]
+        self._cotangent(lam, "lam")
         out = [torch.empty((self.ly, self.lx), dtype=torch.float64, device=self.device) for _ in range(4)]
         self._check(self.lib.lbm_init_vjp(self.ctx, *[_ptr(t) for t in f], _ptr(lam), *[_ptr(t) for t in out]))
         self._keep = f
         return tuple(out)
 
     def check_finite(self, f: torch.Tensor | None = None) -> bool:
+        self._opt_state(f, "f")
         ok = ctypes.c_int(0)
         self._check(self.lib.lbm_check_finite(self.ctx, _ptr(f), ctypes.byref(ok)))
         return bool(ok.value)

@@ -425,6 +425,29 @@ def test_step_from_equals_step():
     np.testing.assert_array_equal(dst[:, 3:-3].cpu().numpy(), lat.state()[:, 3:-3].cpu().numpy())
 
 
+def test_host_or_mistyped_tensors_are_refused_before_any_launch():
+    # The binding checks every tensor it hands to a kernel; nothing reaches
+    # the device, and the lattice steps normally afterwards.
+    lat = Lattice(16, 12, tau=0.8)
+    host = torch.zeros(lat.shape, dtype=torch.float64)
+    dev = lat.new_state(0.1)
+    with pytest.raises(ValueError):
+        lat.step_from(host, lat.new_state())
+    with pytest.raises(ValueError):
+        lat.propagate_bc(host)
+    with pytest.raises(ValueError):
+        lat.adjoint_step(dev, host)
+    with pytest.raises(ValueError):
+        lat.adjoint_step(dev.float(), lat.new_cotangent(0.0))
+    with pytest.raises(ValueError):
+        lat.moments(host)
+    with pytest.raises(ValueError):
+        lat.check_finite(dev[:, :, :8])
+    rho, ux, uy, T = synth.random_fields(16, 12, 5)
+    lat.init(rho, ux, uy, T).step(2)
+    assert lat.status() == 0 and lat.check_finite()
+
+
 # ---------------------------------------------------------------------------
 # FP32 shifted storage: the TMA-staged step against the plain-load step.
 
