@@ -6,16 +6,18 @@ every case below plants one mistake into the oracle for the duration of the
 test (monkeypatch; the oracle's files are not touched) and runs the pins that
 should catch it; at least one of them has to fail.  The mistakes are the kind
 a restatement of the model gets wrong: a sign, a coefficient, a direction, an
-index, a missing normalisation, a transposed operand.
+index, a scale factor, a transposed operand.
 """
 import numpy as np
 import pytest
 
-from oracle import adjoint as A, model as M
+from oracle import adjoint as A, model as M, observables as O
 
 import test_oracle_adjoint as pa
 import test_oracle_bruteforce as pb
 import test_oracle_model as pm
+import test_oracle_observables as po
+import test_oracle_regularized as pr
 
 K = M.K()
 D = M.D
@@ -133,6 +135,41 @@ def propagate_bc_transpose_wrong_wall_column(mu, p):
 ORIG_T = A.propagate_bc_transpose
 
 
+def observables_fields_wrong_half_impulse(f, p):
+    """The mid-step velocity with + g / 2 taken off instead of added."""
+    rho, ux, uy, T = M.moments(M.physical(f))
+    return rho, ux, uy - 0.5 * p.g, T
+
+
+def hermite_project_order3_over_3(fp):
+    """The order-3 term of the projection divided by 3 instead of 3! = 6."""
+    H1, H2, H3, H4 = M._hermite_stack()
+    a0 = fp.sum(axis=0)
+    a1 = np.einsum("p...,pi->...i", fp, H1)
+    a2 = np.einsum("p...,pij->...ij", fp, H2)
+    a3 = np.einsum("p...,pijk->...ijk", fp, H3)
+    a4 = np.einsum("p...,pijkm->...ijkm", fp, H4)
+    out = (a0[None]
+           + np.einsum("...i,pi->p...", a1, H1)
+           + np.einsum("...ij,pij->p...", a2, H2) / 2.0
+           + np.einsum("...ijk,pijk->p...", a3, H3) / 3.0
+           + np.einsum("...ijkm,pijkm->p...", a4, H4) / 24.0)
+    w = K["w"].reshape((M.NPOP,) + (1,) * (fp.ndim - 1))
+    return w * out
+
+
+def collide_regularized_wrong_factor(ft, p):
+    """The projected non-equilibrium part scaled by 1 - tau instead of 1 - 1/tau."""
+    out = np.full_like(ft, np.nan)
+    fp = M.physical(ft)
+    rho, ux, uy, T = M.moments(fp)
+    uys = uy - p.tau * p.g
+    Ts = T + p.tau * (1.0 - p.tau) * p.g * p.g / D
+    feq = M.equilibrium(rho, ux, uys, Ts)
+    out[:, M.HALO:-M.HALO, :] = feq + (1.0 - p.tau) * M.hermite_project(fp - feq)
+    return out
+
+
 # --- the pins that should catch each mistake ---------------------------------
 
 def brute():
@@ -166,6 +203,12 @@ CASES = [
     ("wall cotangent pushed to the mirrored column", (A, "propagate_bc_transpose",
                                                       propagate_bc_transpose_wrong_wall_column),
      [lambda: pa.test_propagate_bc_transpose_dot_product(False)]),
+    ("mid-step velocity correction sign", (O, "fields", observables_fields_wrong_half_impulse),
+     [po.test_free_fall_midpoint_velocity]),
+    ("order-3 weight of the Hermite projection", (M, "hermite_project", hermite_project_order3_over_3),
+     [pr.test_projection_keeps_moments_to_order_4, pr.test_projection_is_idempotent_and_keeps_equilibrium]),
+    ("relaxation factor of the regularised collide", (M, "collide_regularized", collide_regularized_wrong_factor),
+     [pr.test_regularized_equals_bgk_inside_the_hermite_space]),
 ]
 
 
@@ -192,3 +235,6 @@ def test_pins_pass_on_the_oracle_as_it_stands():
     pm.test_propagate_moves_population_along_its_velocity(False)
     pa.test_adjoint_step_dot_product_against_complex_step_jvp()
     pa.test_propagate_bc_transpose_dot_product(False)
+    po.test_free_fall_midpoint_velocity()
+    pr.test_projection_keeps_moments_to_order_4()
+    pr.test_regularized_equals_bgk_inside_the_hermite_space()
