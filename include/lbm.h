@@ -288,6 +288,15 @@ int lbm_status(lbm_ctx* ctx);
 int lbm_constants(const lbm_ctx* ctx, double* r, double* w37,
                   double* q_bottom37, double* q_top37);
 
+/* The same constants without a context, for the lattice parameters *p: the
+ * quadrature (velocity set and weights of the D2Q37 model, Sect. 2) and the
+ * wall ratios of the thermal walls at p->t_bottom and p->t_top (bc, Sect. 2),
+ * all derived on the host.  No device work and no allocation: callable on a
+ * machine without a GPU.  Returns LBM_ERR_INVALID for invalid parameters (as
+ * lbm_create would); any output pointer may be NULL. */
+int lbm_model_constants(const lbm_params* p, double* r, double* w37,
+                        double* q_bottom37, double* q_top37);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,7 @@ SIGNATURES = {
     "lbm_check_finite": (c_int, [c_void_p, c_void_p, P(c_int)]),
     "lbm_status": (c_int, [c_void_p]),
     "lbm_constants": (c_int, [c_void_p, P(c_double), P(c_double), P(c_double), P(c_double)]),
+    "lbm_model_constants": (c_int, [P(LbmParams), P(c_double), P(c_double), P(c_double), P(c_double)]),
     "lbm_probe_fma": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
     "lbm_batch_tile_count": (c_int, []),
     "lbm_batch_tile_per_lattice": (c_int, [c_int]),

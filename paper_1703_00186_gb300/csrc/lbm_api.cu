@@ -417,4 +417,21 @@ int lbm_constants(const lbm_ctx* c, double* r, double* w37, double* q_bottom37, 
   return LBM_OK;
 }
 
+int lbm_model_constants(const lbm_params* p, double* r, double* w37, double* q_bottom37, double* q_top37) {
+  if (!p) return LBM_ERR_INVALID;
+  LatticeArgs a;
+  char err[256];
+  const int rc = make_lattice_args(*p, &a, err, sizeof err);
+  if (rc != LBM_OK) return rc;
+  const Quadrature* q = quadrature(err, sizeof err);
+  if (!q) return LBM_ERR_INVALID;
+  if (r) *r = q->r;
+  for (int l = 0; l < NPOP; ++l) {
+    if (w37) w37[l] = q->w[l];
+    if (q_bottom37) q_bottom37[l] = a.q_bot[l];
+    if (q_top37) q_top37[l] = a.q_top[l];
+  }
+  return LBM_OK;
+}
+
 }  // extern "C"

@@ -81,3 +81,25 @@ def test_oversized_lattices_are_refused(lib):
     tall = L.LbmParams(8, 4 * 65535 + 1, L.LBM_FP64, 0, 0.8, 0.0, 1.0, 1.0, 1.0)
     assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(tall), ctypes.c_void_p(8), ctypes.c_void_p(16),
                           lib.lbm_state_bytes(ctypes.byref(tall)), None) == L.LBM_ERR_INVALID
+
+
+def test_host_constants_match_the_oracle_bit_for_bit(lib):
+    # The library's host-side derivations (the quadrature solved by Newton in
+    # double-double, the wall ratios) against the oracle's 60-digit solve,
+    # rounded once to float64 on both sides: equal bit for bit.
+    import numpy as np
+    from oracle import lattice, model as M
+    from paper_1703_00186_gb300 import _lib as L
+    K = lattice.constants()
+    for t_top, t_bottom in ((0.5, 1.5), (1.0, 1.0), (0.75, 1.25), (1.3, 0.6)):
+        p = L.LbmParams(16, 12, L.LBM_FP64, 0, 0.8, 1e-4, t_top, t_bottom, 1.0)
+        r = ctypes.c_double()
+        w, qb, qt = [(ctypes.c_double * 37)() for _ in range(3)]
+        assert lib.lbm_model_constants(ctypes.byref(p), ctypes.byref(r), w, qb, qt) == L.LBM_OK
+        assert r.value == K["r"]
+        np.testing.assert_array_equal(np.array(w[:]), K["w"])
+        np.testing.assert_array_equal(np.array(qb[:]), M.wall_q(t_bottom, "bottom"))
+        np.testing.assert_array_equal(np.array(qt[:]), M.wall_q(t_top, "top"))
+    bad = L.LbmParams(16, 12, L.LBM_FP64, 0, 0.5, 0.0, 1.0, 1.0, 1.0)
+    assert lib.lbm_model_constants(ctypes.byref(bad), None, None, None, None) == L.LBM_ERR_INVALID
+    assert lib.lbm_model_constants(None, None, None, None, None) == L.LBM_ERR_INVALID
