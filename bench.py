@@ -381,6 +381,14 @@ def batch_study(steps, torch, lattices=64, tile=-1):
             "state_bytes": 2 * 37 * 4 * sum(sp.lx * (sp.ly + 6) for sp in specs)}
 
 
+def workload_config(lx, ly, world):
+    """The `config` object of both arms' JSON lines (the same workload)."""
+    return {"workload": WORKLOAD, "lx": lx, "ly": ly, "sites": lx * ly, "tau": 0.6, "g": 1e-5,
+            "modes": 32, "seed": 0, "t_top": 0.5, "t_bottom": 1.5,
+            "l2": "inputs larger than L2 (state 2 x %.2f GB)" % (37 * (ly + 6) * lx * 8 / 1e9),
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -407,8 +415,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "lx": args.lx, "ly": args.ly,
-                                            "sample_columns": width},
+            "data": "synthetic", "config": workload_config(args.lx, args.ly, args.gpus),
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "cores_available": len(os.sched_getaffinity(0)),
                              "sample": f"{width}x{args.ly} column slab of the RT lattice per step, NumPy float64"},
@@ -654,11 +661,7 @@ def main():
 
     res = {"metric": METRIC, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": WORKLOAD, "lx": lx, "ly": ly, "sites": sites, "tau": 0.6, "g": 1e-5,
-                      "modes": 32, "seed": 0, "t_top": 0.5, "t_bottom": 1.5,
-                      "l2": "inputs larger than L2 (state 2 x %.2f GB)" % (37 * (ly + 6) * lx * 8 / 1e9),
-                      "parallelism": f"replicas x{world}"}}
+           "data": "synthetic", "config": workload_config(lx, ly, world)}
     if "fp64" in out:
         f64 = out["fp64"]
         t_launch = f64["ms"] / K * 1e-3
