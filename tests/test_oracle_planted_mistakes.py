@@ -18,6 +18,7 @@ import test_oracle_bruteforce as pb
 import test_oracle_model as pm
 import test_oracle_observables as po
 import test_oracle_regularized as pr
+import test_oracle_transport as pt
 
 K = M.K()
 D = M.D
@@ -183,7 +184,9 @@ def gravity_pin():
 CASES = [
     ("gravity sign", (M, "collide", collide_variant(gsign=-1.0)), [gravity_pin, brute]),
     ("temperature shift sign", (M, "collide", collide_variant(tsign=-1.0)), [gravity_pin, brute]),
-    ("relaxation by tau instead of 1/tau", (M, "collide", collide_variant(rate=lambda tau: tau)), [brute]),
+    ("relaxation by tau instead of 1/tau", (M, "collide", collide_variant(rate=lambda tau: tau)),
+     [brute, lambda: pt.test_shear_wave_decays_at_the_bgk_viscosity(0.8, 0.7),
+      lambda: pt.test_entropy_wave_decays_at_the_bgk_thermal_diffusivity(0.8, 0.7)]),
     ("cu^4 coefficient", (M, "equilibrium", equilibrium_cu4_over_12),
      [pm.test_equilibrium_moments_are_maxwellian_to_order_4, pm.test_equilibrium_closed_form_equals_hermite_tensor_sum,
       brute]),
