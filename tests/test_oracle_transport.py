@@ -28,7 +28,7 @@ T = 1 make the theta-dependent terms of the equilibrium take part.
 import numpy as np
 import pytest
 
-from oracle import lattice, model as M
+from oracle import lattice, model as M, observables as O
 
 R = lattice.constants()["r"]
 LX, LY, T1, T2 = 4, 64, 50, 250
@@ -93,3 +93,25 @@ def test_density_wave_oscillates_at_the_adiabatic_sound_speed(tau, T0):
     omega = np.pi / np.diff(zero).mean()
     cs = np.sqrt((M.D + 2) / M.D * T0) / R
     assert abs(omega / (cs * 2 * np.pi / LY) - 1) < TOL, omega / (cs * 2 * np.pi / LY) - 1
+
+
+@pytest.mark.parametrize("tau,g,T0", [(0.8, 1e-3, 1.0), (1.0, 1e-3, 1.2)])
+def test_gravity_between_isothermal_walls_settles_into_the_isothermal_atmosphere(tau, g, T0):
+    # Walls at one temperature T0 and gravity g along -y: the steady state is
+    # hydrostatic, dp/dy = -rho g with p = rho T0, so rho ~ exp(-g y / T0)
+    # (y in the length units of c = r xi: a slope of -g r / T0 per site), at
+    # rest (mid-step velocity zero) and at the walls' temperature.  Checked in
+    # the bulk rows after 1500 steps (settled to about 0.3 %).
+    ly, lx = 32, 4
+    z = np.zeros((ly, lx))
+    f = M.init_state(z + 1.0, z, z, z + T0)
+    p = M.Params(lx, ly, tau=tau, g=g, t_top=T0, t_bottom=T0)
+    for _ in range(1500):
+        f = M.step(f, p)
+    rho, ux, uy_mid, T = O.fields(f, p)
+    bulk = slice(8, ly - 8)
+    slope = np.polyfit(np.arange(ly)[bulk], np.log(rho.mean(axis=1))[bulk], 1)[0]
+    assert abs(slope / (-g * R / T0) - 1) < 1e-2, slope / (-g * R / T0) - 1
+    assert np.abs(uy_mid[bulk]).max() < 1e-2 * g / 2
+    assert np.abs(ux).max() < 1e-12
+    assert np.abs(T[bulk] / T0 - 1).max() < 1e-3
