@@ -102,9 +102,10 @@ __device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (do
 // pattern.  hi is x rounded to float32 (half-up on the 29 dropped mantissa
 // bits; the carry runs into the exponent field); the remainder x - hi is an
 // exact integer multiple of 2^(e - 1075), |multiple| <= 2^28, and lo is its
-// float32 rounding.  Representation error <= 2^-48 |x|.  |x| < 2^-126 gives 0;
-// |x| >= 2^128 (beyond float32) or non-finite x gives NaN, so a diverged state
-// stays visible.
+// float32 rounding.  Representation error <= 2^-48 |x| for |x| >= 2^-74; below
+// that lo would be subnormal and is dropped (error <= 2^-24 |x|, at most
+// 2^-98 in absolute terms).  |x| < 2^-126 gives 0; |x| >= 2^128 (beyond
+// float32) or non-finite x gives NaN, so a diverged state stays visible.
 __device__ __forceinline__ DF df_from_double_bits(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
