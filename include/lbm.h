@@ -9,7 +9,7 @@
  * executed as propagate, then bc, then collide (Sect. 2), fused into one
  * CUDA kernel per step for sm_103a.
  *
- * Model readings where the paper is silent (also in the design notes):
+ * Model readings where the paper is silent:
  *  - Velocity set: the 37 integer vectors xi with |xi_x|,|xi_y| <= 3 and
  *    |xi|^2 in {0,1,2,4,5,8,9,10}; c_l = r xi_l, with r and the shell weights
  *    solved from the order-8 Gaussian isotropy conditions.

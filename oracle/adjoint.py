@@ -13,7 +13,7 @@ after propagate, Sect. 2), so for a cotangent lam on the output
   complex-step derivative  dF/dx = Im F(x + i h) / h  (h = 1e-30; no
   subtractive cancellation, exact to rounding) in each of the 37 directions.
 
-Readings for the adjoint study (listed in the design notes):
+Readings for the adjoint study:
 * loss J = mean over physical sites of (T_final - T_target)^2;
 * the control is a per-site initial temperature perturbation dT0, with
   f_0 = f^eq(rho_0, 0, T_0 + dT0) and rho_0 held fixed.

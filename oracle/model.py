@@ -16,7 +16,7 @@ State layout (shared interface with the library, documented in its header):
 above the ly physical rows), x in 0..lx-1 periodic.  Halo rows are never read
 as data; the oracle fills them with NaN so that any leak shows.
 
-Readings where the paper is silent (each is also listed in the design notes):
+Readings where the paper is silent:
 
 1. Equilibrium: the 4th-order Hermite expansion of the Maxwellian about the
    lattice reference temperature 1 (theta = T - 1):
