@@ -40,7 +40,7 @@ WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-
 
 # Algorithmic float64 work of the fused step per site, counted from the
 # collide's formulation (an FMA counts 2 flops), and the FP64 instructions per
-# site that ncu measured for the current kernel (profiles/step_kernel_fp64_*).
+# site that ncu measured for the current kernel (one 2048 x 1024 launch).
 # 110 of the 540 flops are the moment sums, which the kernel forms exactly in
 # fixed point on the integer pipe (one rounding per sum) instead of with FP64
 # additions.
