@@ -41,6 +41,20 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_library_exports_no_undeclared_entry_point(lib):
+    # every exported lbm_* function is declared (and so documented) in include/
+    import shutil
+    import subprocess
+    from paper_1703_00186_gb300 import _lib as L
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--defined-only", L.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = {ln.split()[-1] for ln in out.stdout.splitlines() if ln.split() and ln.split()[-1].startswith("lbm_")}
+    assert exported, "no lbm_* symbols found"
+    assert exported <= declared_functions(), sorted(exported - declared_functions())
+
+
 def test_state_bytes_and_argument_checks_need_no_gpu(lib):
     from paper_1703_00186_gb300 import _lib as L
     p = L.LbmParams(64, 128, L.LBM_FP64, 0, 0.8, 1e-4, 0.5, 1.5, 1.0)
