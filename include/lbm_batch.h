@@ -65,7 +65,14 @@ int lbm_batch_tile_per_lattice(int i);
  * LBM_FP32_SHIFTED).  descs is a host array of n entries.  stream: cudaStream_t. */
 int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int precision,
                      void* stream);
+
+/* Synchronise the batch's stream, then release its device tables, streams
+ * and graphs (the caller's lattice buffers are untouched).  NULL is
+ * accepted. */
 void lbm_batch_destroy(lbm_batch* b);
+
+/* Message of the last failed call on b (never NULL; owned by the batch;
+ * "null batch" for b == NULL). */
 const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* Lattice i := f^eq(rho, u, T) (device fields [ly_i][lx_i]). */
