@@ -106,7 +106,27 @@ enum {
    * ignored).  Bit-identical results.  Measured slower than the default on
    * GB300 (the per-tile block barrier costs more issue slots than the load
    * latency it hides); kept for comparison. */
-  LBM_FLAG_TMA_LOADS = 4
+  LBM_FLAG_TMA_LOADS = 4,
+  /* Arithmetic of the LBM_FP32_SHIFTED collide (at most one of the two; the
+   * storage, every other call and the adjoint are unchanged):
+   *   (neither)                 the default: split moment sums, double-float
+   *                             density and temperature terms, float32
+   *                             coefficients and polynomial, and the
+   *                             conserved-moment correction (see LBM_FP32_SHIFTED);
+   *   LBM_FLAG_FP32_F64_TERMS   the conserved-moment sums of eq. (2) exact
+   *                             (rounded once to float64) on the populations
+   *                             w_l rho0 + d_l, the site fields and every
+   *                             temperature-dependent equilibrium term (the
+   *                             per-shell coefficients and the zeroth-order
+   *                             deviation w (rho A0 - rho0)) in float64, each
+   *                             rounded once to float32; the cu-dependent
+   *                             polynomial and the relaxation in float32; no
+   *                             correction;
+   *   LBM_FLAG_FP32_F64_COLLIDE the LBM_FP64 collide on the decoded
+   *                             populations, re-encoded to float32: the error
+   *                             of the float32 storage alone. */
+  LBM_FLAG_FP32_F64_TERMS = 8,
+  LBM_FLAG_FP32_F64_COLLIDE = 16
 };
 
 typedef struct lbm_params {

@@ -25,6 +25,8 @@ LBM_FP64_DF = 2
 LBM_FLAG_PERIODIC_Y = 1
 LBM_FLAG_REGULARIZED = 2
 LBM_FLAG_TMA_LOADS = 4
+LBM_FLAG_FP32_F64_TERMS = 8
+LBM_FLAG_FP32_F64_COLLIDE = 16
 LBM_PATH_PLAIN = 0
 LBM_PATH_TMA = 1
 LBM_NOALLOC_MAX_LX = 16384

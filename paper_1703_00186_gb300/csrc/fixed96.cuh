@@ -98,6 +98,37 @@ __device__ __forceinline__ Fix96 to_fix(double v, bool& ok) {
   return r;
 }
 
+// Exact conversion of a float32 with |v| < 4 (biased exponent <= 128):
+// v = M 2^(e - 150) for the 24-bit significand M, i.e. M shifted left by
+// e - 68 <= 60 places on the 2^-82 grid.  Values below 2^-58 keep their bits
+// down to 2^-82 (the rest is dropped); zero gives 0.  `ok` is cleared for
+// |v| >= 4, infinities and NaNs.  Integer operations only.
+__device__ __forceinline__ Fix96 to_fix_f32(float v, bool& ok) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xffu);
+  ok = ok && e <= 128;
+  const unsigned m = (b & 0x7fffffu) | (e != 0 ? 0x800000u : 0u);
+  const int s = (e != 0 ? e : 1) - 68;
+  Fix96 r;
+  if (s >= 32) {
+    const int t = min(s - 32, 31);  // t <= 28 while ok
+    r.w0 = 0u;
+    r.w1 = m << t;
+    r.w2 = __funnelshift_l(m, 0u, t);
+  } else if (s >= 0) {
+    r.w0 = m << s;
+    r.w1 = __funnelshift_l(m, 0u, s);
+    r.w2 = 0u;
+  } else {
+    const int t = -s;
+    r.w0 = t < 24 ? m >> t : 0u;
+    r.w1 = 0u;
+    r.w2 = 0u;
+  }
+  if (b >> 31) r = fix_sub(Fix96{0u, 0u, 0u}, r);
+  return r;
+}
+
 // Round to the nearest float64 (ties to even).  The magnitude is below 2^95.
 __device__ __forceinline__ double fix_to_double(Fix96 a) {
   const unsigned sign = a.w2 & 0x80000000u;

@@ -50,6 +50,27 @@ const Quadrature* quadrature(char* err, size_t errlen) {
 
 size_t element_size(int precision);
 
+// sum_i k_i v_i, exactly, as a 96-bit two's-complement number on the 2^-82
+// grid (words w0, w1, w2 as the device's Fix96), for float64 values |v_i| < 4
+// and small integer weights k_i.  Bits of a value below 2^-82 are dropped.
+static void fix_words(const double* v, const int* k, int n, unsigned out[3]) {
+  __int128 acc = 0;
+  for (int i = 0; i < n; ++i) {
+    if (v[i] == 0.0 || k[i] == 0) continue;
+    int e = 0;
+    const double m = std::frexp(std::fabs(v[i]), &e);         // |v| = m 2^e, m in [0.5, 1)
+    const long long M = (long long)std::ldexp(m, 53);          // exact 53-bit integer
+    const int sh = e - 53 + 82;                                // |v| 2^82 = M 2^sh
+    __int128 t = sh >= 0 ? ((__int128)M << sh) : (sh > -64 ? (__int128)(M >> -sh) : 0);
+    if (v[i] < 0) t = -t;
+    acc += t * k[i];
+  }
+  const unsigned __int128 u = (unsigned __int128)acc;
+  out[0] = (unsigned)(u & 0xffffffffu);
+  out[1] = (unsigned)((u >> 32) & 0xffffffffu);
+  out[2] = (unsigned)((u >> 64) & 0xffffffffu);
+}
+
 // Fill the per-launch constants of a lattice.  Returns 0 or an error code
 // with a message in err.
 int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t errlen) {
@@ -70,8 +91,14 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     std::snprintf(err, errlen, "invalid physical parameters (need tau > 0.5, finite g, T_wall > 0)");
     return LBM_ERR_INVALID;
   }
-  if (p.flags & ~(LBM_FLAG_PERIODIC_Y | LBM_FLAG_REGULARIZED | LBM_FLAG_TMA_LOADS)) {
+  if (p.flags & ~(LBM_FLAG_PERIODIC_Y | LBM_FLAG_REGULARIZED | LBM_FLAG_TMA_LOADS | LBM_FLAG_FP32_F64_TERMS |
+                  LBM_FLAG_FP32_F64_COLLIDE)) {
     std::snprintf(err, errlen, "unknown flags 0x%x", p.flags);
+    return LBM_ERR_INVALID;
+  }
+  const int f32_flags = p.flags & (LBM_FLAG_FP32_F64_TERMS | LBM_FLAG_FP32_F64_COLLIDE);
+  if (f32_flags && (p.precision != LBM_FP32_SHIFTED || f32_flags == (LBM_FLAG_FP32_F64_TERMS | LBM_FLAG_FP32_F64_COLLIDE))) {
+    std::snprintf(err, errlen, "LBM_FLAG_FP32_F64_TERMS / _COLLIDE: one of them, LBM_FP32_SHIFTED only");
     return LBM_ERR_INVALID;
   }
   if ((p.flags & LBM_FLAG_REGULARIZED) && p.precision != LBM_FP64) {
@@ -95,6 +122,9 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->periodic_y = (p.flags & LBM_FLAG_PERIODIC_Y) ? 1 : 0;
   a->regularized = (p.flags & LBM_FLAG_REGULARIZED) ? 1 : 0;
   a->tma_loads = (p.flags & LBM_FLAG_TMA_LOADS) ? 1 : 0;
+  a->fp32_arith = (p.flags & LBM_FLAG_FP32_F64_TERMS)     ? FP32_ARITH_F64_TERMS
+                  : (p.flags & LBM_FLAG_FP32_F64_COLLIDE) ? FP32_ARITH_F64_COLLIDE
+                                                          : FP32_ARITH_SPLIT;
   a->tau = p.tau;
   a->g = p.g;
   a->omega = 1.0 / p.tau;
@@ -123,6 +153,22 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     a->w_rho0[l] = q->w[l] * p.rho0;
     a->w_rho0_f[l] = (float)a->w_rho0[l];
   }
+  {
+    // exact sums of the shift constants on the 2^-82 grid (see fix_words)
+    double v_rho[NPOP], v_exi[NPOP];
+    for (int l = 0; l < NPOP; ++l) {
+      v_rho[l] = a->w_rho0[l];
+      v_exi[l] = a->w_rho0[l];
+    }
+    int one[NPOP], c2[NPOP];
+    for (int l = 0; l < NPOP; ++l) {
+      one[l] = 1;
+      c2[l] = sq(l);
+    }
+    fix_words(v_rho, one, NPOP, a->fix_shift_rho);
+    fix_words(v_exi, c2, NPOP, a->fix_shift_exi);
+  }
+  for (int j = 0; j < NSHELL; ++j) a->ow_shell[j] = a->omega * q->w_shell[j];
   for (int j = 0; j < NSHELL; ++j) {
     a->w_shell_f[j] = (float)q->w_shell[j];
     a->c2_shell_f[j] = (float)q->c2_shell[j];

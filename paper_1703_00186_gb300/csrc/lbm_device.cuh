@@ -529,6 +529,76 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
   }
 }
 
+// Exact moment sums of the populations w_rho0[l] + d_l held as float32
+// deviations d_l: the deviations convert exactly to 96-bit fixed point from
+// their bit patterns (integer pipe only), the shift constants enter as their
+// exact sums precomputed on the host, and each sum is rounded once to
+// float64.  Returns false, leaving `mo` unset, when a deviation is outside
+// the fixed-point range (|d| >= 4, infinities, NaN).
+__device__ __forceinline__ bool moment_sums_f32_exact(const float (&d)[NPOP], const LatticeArgs& a, Moments& mo) {
+  bool ok = true;
+  Fix96 r = fix_add(Fix96{a.fix_shift_rho[0], a.fix_shift_rho[1], a.fix_shift_rho[2]}, to_fix_f32(d[0], ok));
+  Fix96 jx{0u, 0u, 0u}, jy{0u, 0u, 0u};
+  Fix96 e{a.fix_shift_exi[0], a.fix_shift_exi[1], a.fix_shift_exi[2]};
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const Fix96 p = to_fix_f32(d[2 * k + 1], ok), m = to_fix_f32(d[2 * k + 2], ok);
+    const Fix96 s = fix_add(p, m), df = fix_sub(p, m);
+    r = fix_add(r, s);
+    e = fix_axpy(e, s, rep_x(k) * rep_x(k) + rep_y(k) * rep_y(k));
+    jx = fix_axpy(jx, df, rep_x(k));
+    jy = fix_axpy(jy, df, rep_y(k));
+  }
+  if (!ok) return false;
+  mo.rho = fix_to_double(r);
+  mo.Jx = fix_to_double(jx);
+  mo.Jy = fix_to_double(jy);
+  mo.Exi = fix_to_double(e);
+  return true;
+}
+
+// BGK collide on float32 deviations with the conserved-moment sums and the
+// temperature-dependent equilibrium terms in float64 (LBM_FLAG_FP32_F64_TERMS):
+//  * rho, J, E of eq. (2): exact sums of the populations w_rho0[l] + d_l,
+//    rounded once (moment_sums_f32_exact);
+//  * rho, u, T, the gravity shift, the Hermite coefficients B and, per shell,
+//    A0, A1, A2 and the zeroth-order deviation omega w (rho A0 - rho0): float64,
+//    A1, A2 and the deviation rounded once to float32;
+//  * the cu-dependent polynomial and the relaxation: float32, as in
+//    collide_fp32.
+// No conserved-moment correction.  Sites with a deviation outside the
+// fixed-point range take float64 sums of the decoded populations.
+__device__ __forceinline__ void collide_fp32_f64terms(float (&d)[NPOP], const LatticeArgs& a) {
+  Moments mo;
+  if (!moment_sums_f32_exact(d, a, mo)) mo = site_moments([&](int l) { return a.w_rho0[l] + (double)d[l]; });
+  const SiteFields sf = site_fields(mo, a);
+  const double theta = sf.T + a.tshift;
+  const double uys = sf.uy - a.tau_g_xi;
+  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
+  const EqCoef B = eq_coef(U2, theta);
+  const double th2 = theta * theta;
+  const float v_x = (float)(a.r2 * sf.ux), v_y = (float)(a.r2 * uys);
+  const float wr = (float)(a.omega * sf.rho);
+  const float omc = a.omc_f;
+  d[0] = fmaf(omc, d[0], (float)(a.ow_shell[0] * fma(sf.rho, B.B00, -a.rho0)));
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int j = pair_shell(k);
+    const double A0 = fma(a.c4e_shell[j], th2, fma(a.c2_shell[j], B.B01, B.B00));
+    const float A1 = (float)fma(theta, a.c2h_shell[j], B.B10);
+    const float A2 = (float)fma(theta, a.c2q_shell[j], B.B20);
+    const float beta = (float)(a.ow_shell[j] * fma(sf.rho, A0, -a.rho0));  // omega w (rho A0 - rho0)
+    const float alpha = wr * a.w_shell_f[j];                               // omega w rho
+    const float cu = pair_cu<float>(k, v_x, v_y);
+    const float cu2 = cu * cu;
+    const float E = fmaf(alpha * cu2, fmaf(cu2, 1.0f / 24.0f, A2), beta);
+    const float O = alpha * cu * fmaf(cu2, 1.0f / 6.0f, A1);
+    const float2 D = fma2(f2s(omc), f2(d[2 * k + 1], d[2 * k + 2]), f2(E + O, E - O));
+    d[2 * k + 1] = D.x;
+    d[2 * k + 2] = D.y;
+  }
+}
+
 // Per-pair constants for rolled loops: representative R_k and shell index.
 static __constant__ signed char c_pair_rep[NPAIR][2] = {
     {1, 0}, {0, 1}, {1, 1}, {-1, 1}, {2, 0}, {0, 2}, {2, 1}, {1, 2}, {-1, 2},

@@ -121,6 +121,18 @@ struct LatticeArgs {
   int tma_loads;              // LBM_FLAG_TMA_LOADS
   long long pull_off[NPOP];   // (l plane - xi_ly lx - xi_lx) * element size
   long long plane_off[NPOP];  // l plane * element size
+  // Arithmetic of the LBM_FP32_SHIFTED collide: FP32_ARITH_SPLIT (default),
+  // FP32_ARITH_F64_TERMS (LBM_FLAG_FP32_F64_TERMS) or FP32_ARITH_F64_COLLIDE
+  // (LBM_FLAG_FP32_F64_COLLIDE).
+  int fp32_arith;
+  double ow_shell[NSHELL];    // omega w_j
+  // Exact sums of the shift constants w_rho0[l] (rho) and |xi_l|^2 w_rho0[l]
+  // (Exi) as 96-bit two's-complement fixed point on the 2^-82 grid (words
+  // w0, w1, w2); the momentum sums of the shift vanish exactly (+- pairs).
+  unsigned fix_shift_rho[3];
+  unsigned fix_shift_exi[3];
 };
+
+enum { FP32_ARITH_SPLIT = 0, FP32_ARITH_F64_TERMS = 1, FP32_ARITH_F64_COLLIDE = 2 };
 
 }  // namespace lbm

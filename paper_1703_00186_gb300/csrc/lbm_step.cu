@@ -46,7 +46,7 @@ struct Codec<LBM_FP32_SHIFTED> {
 // it at 96 registers (5 blocks per SM, some spills) measured 27% faster than
 // the unconstrained 163 registers (3 blocks).  The double-float collide gains
 // 2-3% from the same cap (60 bytes of spill, 4 -> 5 blocks per SM).
-template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false>
+template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, int F32M = FP32_ARITH_SPLIT>
 __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a) {
   using T = typename Codec<PREC>::T;
@@ -77,6 +77,15 @@ __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel
   if (COLLIDE) {
     if constexpr (PREC == LBM_FP64) {
       collide_fp64(f, a);
+    } else if constexpr (F32M == FP32_ARITH_F64_TERMS) {
+      collide_fp32_f64terms(f, a);
+    } else if constexpr (F32M == FP32_ARITH_F64_COLLIDE) {
+      double g[NPOP];
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) g[l] = codec(l, f[l]);
+      collide_fp64(g, a);
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) f[l] = codec.enc(l, g[l]);
     } else {
       collide_fp32(f, a);
     }
@@ -392,7 +401,7 @@ static bool tma_launch_shape(int dev, int* ctas) {
 // Whether an FP32-store collide step from `src` runs the TMA-staged kernel.
 bool step_uses_tma(const LatticeArgs& a, const void* src) {
   int dev = 0, ctas = 0;
-  return a.tma_loads && !a.periodic_y && a.idx32 && a.lx % 4 == 0 &&
+  return a.tma_loads && a.fp32_arith == FP32_ARITH_SPLIT && !a.periodic_y && a.idx32 && a.lx % 4 == 0 &&
          (reinterpret_cast<uintptr_t>(src) & 15u) == 0 && tensor_map_encoder() != nullptr &&
          cudaGetDevice(&dev) == cudaSuccess && tma_launch_shape(dev, &ctas);
 }
@@ -442,7 +451,11 @@ cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, cons
     else
       step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a);
   } else {
-    if (collide) {
+    if (collide && a.fp32_arith == FP32_ARITH_F64_TERMS) {
+      step_kernel<LBM_FP32_SHIFTED, true, false, false, FP32_ARITH_F64_TERMS><<<grid, block, 0, s>>>(src, dst, a);
+    } else if (collide && a.fp32_arith == FP32_ARITH_F64_COLLIDE) {
+      step_kernel<LBM_FP32_SHIFTED, true, false, false, FP32_ARITH_F64_COLLIDE><<<grid, block, 0, s>>>(src, dst, a);
+    } else if (collide) {
       const cudaError_t e = launch_step_tma(src, dst, a, s);
       if (e != cudaErrorNotSupported) return e;
       (void)cudaGetLastError();  // a refused set-up call leaves no error behind

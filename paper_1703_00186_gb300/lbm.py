@@ -62,13 +62,19 @@ class Lattice:
 
     State buffers are (37, ly + 6, lx) tensors (three halo rows on each side,
     x fastest); dtype float64, or float32 holding f_l - w_l rho0 when
-    ``precision="fp32"``.
+    ``precision="fp32"``.  ``fp32_arith`` selects the arithmetic of the
+    float32-store collide: "split" (default), "fp64_terms" (float64 moment
+    sums and temperature-dependent equilibrium terms) or "fp64_collide" (the
+    float64 collide on the decoded populations).
     """
+
+    FP32_ARITH = {"split": 0, "fp64_terms": L.LBM_FLAG_FP32_F64_TERMS,
+                  "fp64_collide": L.LBM_FLAG_FP32_F64_COLLIDE}
 
     def __init__(self, lx: int, ly: int, tau: float, g: float = 0.0, t_top: float = 1.0,
                  t_bottom: float = 1.0, precision: str = "fp64", rho0: float = 1.0,
                  periodic_y: bool = False, regularized: bool = False, tma_loads: bool = False,
-                 device=None, stream=None):
+                 fp32_arith: str = "split", device=None, stream=None):
         self.lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -81,7 +87,7 @@ class Lattice:
         prec = {"fp64": L.LBM_FP64, "fp32": L.LBM_FP32_SHIFTED, "fp64df": L.LBM_FP64_DF}[precision]
         self.dtype = torch.float32 if prec == L.LBM_FP32_SHIFTED else torch.float64
         flags = ((L.LBM_FLAG_PERIODIC_Y if periodic_y else 0) | (L.LBM_FLAG_REGULARIZED if regularized else 0)
-                 | (L.LBM_FLAG_TMA_LOADS if tma_loads else 0))
+                 | (L.LBM_FLAG_TMA_LOADS if tma_loads else 0) | self.FP32_ARITH[fp32_arith])
         self.params = L.LbmParams(self.lx, self.ly, prec, flags,
                                   float(tau), float(g), float(t_top), float(t_bottom), float(rho0))
         self.tau, self.g, self.t_top, self.t_bottom, self.rho0 = tau, g, t_top, t_bottom, rho0

@@ -84,9 +84,19 @@ def test_regularized_flag_only_with_fp64(lib):
     p = L.LbmParams(64, 128, L.LBM_FP32_SHIFTED, L.LBM_FLAG_REGULARIZED, 0.8, 0.0, 1.0, 1.0, 1.0)
     assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(p), ctypes.c_void_p(8), ctypes.c_void_p(16),
                           lib.lbm_state_bytes(ctypes.byref(p)), None) == L.LBM_ERR_INVALID
-    bad = L.LbmParams(64, 128, L.LBM_FP64, 8, 0.8, 0.0, 1.0, 1.0, 1.0)   # unknown flag bit
+    bad = L.LbmParams(64, 128, L.LBM_FP64, 32, 0.8, 0.0, 1.0, 1.0, 1.0)   # unknown flag bit
     assert lib.lbm_create(ctypes.byref(ctx), ctypes.byref(bad), ctypes.c_void_p(8), ctypes.c_void_p(16),
                           lib.lbm_state_bytes(ctypes.byref(bad)), None) == L.LBM_ERR_INVALID
+
+
+def test_fp32_arith_flags_one_at_a_time_and_fp32_only(lib):
+    from paper_1703_00186_gb300 import _lib as L
+    terms, coll = L.LBM_FLAG_FP32_F64_TERMS, L.LBM_FLAG_FP32_F64_COLLIDE
+    for prec, flags, rc in ((L.LBM_FP32_SHIFTED, terms, L.LBM_OK), (L.LBM_FP32_SHIFTED, coll, L.LBM_OK),
+                            (L.LBM_FP32_SHIFTED, terms | coll, L.LBM_ERR_INVALID),
+                            (L.LBM_FP64, terms, L.LBM_ERR_INVALID), (L.LBM_FP64_DF, coll, L.LBM_ERR_INVALID)):
+        p = L.LbmParams(64, 128, prec, flags, 0.8, 1e-5, 0.9, 1.1, 1.0)
+        assert lib.lbm_model_constants(ctypes.byref(p), None, None, None, None) == rc, (prec, flags)
 
 
 def test_oversized_lattices_are_refused(lib):

@@ -1,0 +1,118 @@
+"""The three arithmetics of the float32-store collide on the GPU.
+
+* ``fp64_collide`` (LBM_FLAG_FP32_F64_COLLIDE): the float64 collide between a
+  decode and a round-to-nearest encode, the same computation as the storage
+  oracle ``oracle.storage.step_fp32_storage``.  The float64 step matches the
+  oracle to ~1e-15, so the encoded results agree bit for bit except where
+  the float64 value lies within that distance of a float32 rounding
+  boundary: there they differ by one ulp.
+* ``fp64_terms`` (LBM_FLAG_FP32_F64_TERMS): moment sums and temperature-
+  dependent equilibrium terms in float64, the cu polynomial and relaxation
+  in float32; one step within 2e-6 per plane of the float64 oracle (the
+  float32 quantum of the relaxed deviations), as the default arithmetic.
+* all three keep the density and temperature error flat over 1000 steps of a
+  64 x 128 Rayleigh-Taylor lattice against the float64 step.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lattice, model as M, storage as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1703_00186_gb300.lbm import Lattice
+
+K = lattice.constants()
+ARITHS = ("split", "fp64_terms", "fp64_collide")
+
+
+def to_dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def plane_err(a, b):
+    a, b = M.physical(a), M.physical(b)
+    return (np.abs(a - b).max(axis=(1, 2)) / np.abs(b).max(axis=(1, 2))).max()
+
+
+def noisy_state(lx, ly, seed, eps=0.02):
+    rho, ux, uy, T = synth.random_fields(lx, ly, seed, umax=0.1)
+    f = M.init_state(rho, ux, uy, T)
+    f[:, 3:-3] *= 1.0 + eps * synth.noise(lx, ly, seed + 1)
+    return f
+
+
+def make(p, arith, rho0):
+    return Lattice(p.lx, p.ly, tau=p.tau, g=p.g, t_top=p.t_top, t_bottom=p.t_bottom, precision="fp32",
+                   rho0=rho0, periodic_y=p.periodic_y, fp32_arith=arith)
+
+
+@pytest.mark.parametrize("lx,ly,periodic_y", [(64, 40, False), (67, 45, False), (40, 24, True)])
+def test_fp64_collide_arith_is_the_storage_oracle(lx, ly, periodic_y):
+    rho0 = 1.05
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.8, t_bottom=1.2, periodic_y=periodic_y)
+    d = S.encode(noisy_state(lx, ly, 400 + lx), rho0)
+    lat = make(p, "fp64_collide", rho0)
+    lat.set_state(to_dev(d, torch.float32))
+    lat.step(1)
+    got = M.physical(lat.state().cpu().numpy())
+    want = M.physical(S.step_fp32_storage(d, p, rho0))
+    diff = got != want
+    assert diff.mean() <= 1e-3, diff.mean()
+    if diff.any():
+        ulps = np.abs(got[diff].view(np.int32).astype(np.int64) - want[diff].view(np.int32).astype(np.int64))
+        assert ulps.max() <= 1, ulps.max()
+
+
+def test_fp64_collide_arith_tracks_the_storage_oracle_over_50_steps():
+    rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 3, delta=0.5)
+    rho0 = float(rho.mean())
+    p = M.Params(64, 128, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
+    d = S.encode(M.init_state(rho, ux, uy, T), rho0)
+    lat = make(p, "fp64_collide", rho0)
+    lat.set_state(to_dev(d, torch.float32))
+    lat.step(50)
+    got = S.decode(lat.state().cpu().numpy(), rho0)
+    want = S.decode(S.run_fp32_storage(d, p, rho0, 50), rho0)
+    assert plane_err(got, want) <= 1e-6
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_fp32_arith_one_step_against_the_float64_oracle(arith):
+    lx, ly = 64, 40
+    rho0 = 1.1
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.8, t_bottom=1.2)
+    d = S.encode(noisy_state(lx, ly, 300), rho0)
+    want = M.step(S.decode(d, rho0), p)
+    lat = make(p, arith, rho0)
+    lat.set_state(to_dev(d, torch.float32))
+    lat.step(1)
+    got = S.decode(lat.state().cpu().numpy(), rho0)
+    assert plane_err(got, want) <= 2e-6
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_fp32_arith_error_stays_flat_over_1000_steps(arith):
+    rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 0, delta=0.5)
+    kw = dict(tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
+    a = Lattice(64, 128, precision="fp64", **kw).init(rho, ux, uy, T)
+    b = Lattice(64, 128, precision="fp32", rho0=float(rho.mean()), fp32_arith=arith, **kw).init(rho, ux, uy, T)
+    errs = {}
+    for n in (200, 800):
+        a.step(n)
+        b.step(n)
+        fa = [t.cpu().numpy() for t in a.moments()]
+        fb = [t.cpu().numpy() for t in b.moments()]
+        errs[n] = [np.abs(x - y).max() / np.abs(y).max() for x, y in zip(fb, fa)]
+    for n in (200, 800):
+        assert errs[n][0] <= 1e-6 and errs[n][3] <= 1e-6, errs
+    assert errs[800][0] <= 2.5 * errs[200][0] + 1e-7 and errs[800][3] <= 2.5 * errs[200][3] + 1e-7, errs
+
+
+def test_fp32_arith_flags_are_exclusive_and_fp32_only():
+    from paper_1703_00186_gb300 import _lib as L
+    with pytest.raises(L.LBMError):
+        Lattice(16, 12, tau=0.8, precision="fp64", fp32_arith="fp64_terms")

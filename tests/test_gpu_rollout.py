@@ -56,10 +56,9 @@ def test_checkpoint_spacing_does_not_change_gradient():
     assert np.abs(g1 - g2).max() <= 1e-13 * np.abs(g1).max()
 
 
-def test_rollout_gradient_matches_central_differences_16_directions():
-    p, rho, T, target, dT0 = case(64, 96, seed=11)
-    n, K = 200, 50
-    J, g, lat = gpu_grad(p, rho, T, target, dT0, n, K)
+def _fp64_central_differences(p, rho, T, target, dT0, n, K, dirs, eps=1e-4):
+    """float64 central differences of the float64 GPU rollout along dirs."""
+    lat = Lattice(p.lx, p.ly, tau=p.tau, g=p.g, t_top=p.t_top, t_bottom=p.t_bottom, precision="fp64")
     rho_t = torch.tensor(rho, device="cuda")
     T_t = torch.tensor(T, device="cuda")
     tgt = torch.tensor(target, device="cuda")
@@ -68,14 +67,34 @@ def test_rollout_gradient_matches_central_differences_16_directions():
         with torch.no_grad():
             return float(temperature_loss(torch.tensor(d, device="cuda"), lat, rho_t, T_t, tgt, n, K))
 
-    rng = np.random.default_rng(2024)
-    eps = 1e-4
-    worst = 0.0
-    for _ in range(16):
-        v = rng.standard_normal(dT0.shape)
-        fd = (loss(dT0 + eps * v) - loss(dT0 - eps * v)) / (2 * eps)
-        ad = float((g * v).sum())
-        worst = max(worst, abs(fd - ad) / abs(ad))
+    return [(loss(dT0 + eps * v) - loss(dT0 - eps * v)) / (2 * eps) for v in dirs]
+
+
+def _directions(shape, k=16, seed=2024):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal(shape) for _ in range(k)]
+
+
+def test_rollout_gradient_matches_central_differences_16_directions():
+    p, rho, T, target, dT0 = case(64, 96, seed=11)
+    n, K = 200, 50
+    _, g, _ = gpu_grad(p, rho, T, target, dT0, n, K)
+    dirs = _directions(dT0.shape)
+    fds = _fp64_central_differences(p, rho, T, target, dT0, n, K, dirs)
+    worst = max(abs(fd - float((g * v).sum())) / abs(fd) for fd, v in zip(fds, dirs))
+    assert worst <= 1e-6, worst
+
+
+def test_fp32_store_rollout_gradient_matches_fp64_central_differences_16_directions():
+    # The float32-store rollout's adjoint gradient against float64 central
+    # differences of the float64 rollout: the bar of the adjoint (1e-6
+    # relative) holds for the float32-store variant too.
+    p, rho, T, target, dT0 = case(64, 96, seed=11)
+    n, K = 200, 50
+    _, g, _ = gpu_grad(p, rho, T, target, dT0, n, K, "fp32")
+    dirs = _directions(dT0.shape)
+    fds = _fp64_central_differences(p, rho, T, target, dT0, n, K, dirs)
+    worst = max(abs(fd - float((g * v).sum())) / abs(fd) for fd, v in zip(fds, dirs))
     assert worst <= 1e-6, worst
 
 
