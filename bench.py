@@ -38,15 +38,18 @@ sys.path.insert(0, ROOT)
 METRIC = "D2Q37 MLUPS, FP64 vs FP32-store, and adjoint/forward step time ratio, 1 GB300"
 WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-5"
 
-# Algorithmic float64 work of the fused step per site, counted from the
-# collide's formulation (an FMA counts 2 flops), and the FP64 instructions per
-# site that ncu measured for the current kernel (one 2048 x 1024 launch).
-# 110 of the 540 flops are the moment sums, which the kernel forms exactly in
-# fixed point on the integer pipe (one rounding per sum) instead of with FP64
-# additions.
-FP64_FLOP_PER_SITE = 540
+# Algorithmic float64 work of the fused step per site, counted stage by stage
+# from the collide's formulation (an FMA counts 2 flops, the division 1/rho
+# counts 1): moment sums 110, site fields 9, gravity shift and Hermite
+# coefficients 30, per-shell terms 81, per-pair polynomial and relaxation 312
+# (18 pairs x 16 + 24 for the c.u products).  The 110 of the moment sums run
+# exactly in fixed point on the integer pipe; the other 432 on the FP64 pipe.
+# ncu counts 261 FP64 instructions per site on the current kernel (DFMA 177,
+# DMUL 72, DADD 12: 438 flops, the 432 plus the Newton steps of 1/rho).
+FP64_FLOP_PER_SITE = 542
 FP64_FLOP_PER_SITE_MOMENT_SUMS = 110
 FP64_INSTR_PER_SITE_NCU = 261
+FP64_PIPE_FLOP_PER_SITE_NCU = 2 * 177 + 72 + 12
 # DRAM bytes per site of the float64 step (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of one 2048 x 1024 launch, 1190.35 MB / 2097152 sites;
 # traffic grows with the site count, so a full launch is scaled by sites).
@@ -180,35 +183,67 @@ def barrier(torch, world):
         torch.cuda.synchronize()
 
 
-def cpu_baseline(lx, ly, budget_s):
-    """Time the float64 oracle on a column slab of the workload."""
-    import numpy as np
+def _oracle_worker_init(core):
+    """Spawned oracle worker: one BLAS / OpenMP thread (set before NumPy is
+    imported), pinned to one host core when `core` is given."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    if core is not None:
+        os.sched_setaffinity(0, {core})
+    sys.path.insert(0, ROOT)
 
+
+def _oracle_slab(args):
+    """`steps` float64 oracle steps on columns [x0, x0 + width) of the
+    workload's fields (the slab periodic in x); returns sites x steps."""
+    lx, ly, x0, width, steps = args
     import synth
     from oracle import model as M
     rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 32, 0)
-    width = 32
-    p_probe = M.Params(width, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
-    f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
-    t0 = time.perf_counter()
-    M.step(f, p_probe)
-    per_site = (time.perf_counter() - t0) / (width * ly)
-    # grow the slab so that the sample takes about budget_s
-    width = int(max(32, min(lx, budget_s / max(per_site, 1e-9) / ly / 2)))
+    cols = slice(x0, x0 + width)
     p = M.Params(width, ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
-    f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
-    steps = 2
-    t0 = time.perf_counter()
-    c0 = time.process_time()
+    f = M.init_state(rho[:, cols], ux[:, cols], uy[:, cols], T[:, cols])
     for _ in range(steps):
         f = M.step(f, p)
-    dt = time.perf_counter() - t0
-    cores = (time.process_time() - c0) / dt  # threads NumPy actually kept busy
-    assert np.isfinite(M.physical(f)).all()
-    return {"value": width * ly * steps / dt / 1e6, "unit": "MLUPS", "cores": round(cores, 2),
-            "cores_available": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"{width}x{ly} column slab of the 2048x4096 RT lattice (periodic in x), "
-                      f"{steps} steps, NumPy float64; {dt:.1f} s"}
+    return width * ly * steps
+
+
+def _oracle_throughput(lx, ly, workers, width, steps, pin_one_core=False):
+    """MLUPS of the oracle on `workers` spawned processes, each stepping its own
+    column slab (independent slabs: the oracle's work split over host cores
+    as the paper splits a lattice over nodes).  Spawned, never forked: the
+    parent holds a CUDA context."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    core = sorted(os.sched_getaffinity(0))[0] if pin_one_core else None
+    with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(core,)) as pool:
+        pool.map(_oracle_slab, [(lx, ly, 0, 8, 1)] * workers)  # imports, first-touch
+        jobs = [(lx, ly, (i * width) % max(1, lx - width + 1), width, steps) for i in range(workers)]
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_slab, jobs))
+        dt = time.perf_counter() - t0
+    return done / dt / 1e6, dt
+
+
+def cpu_baseline(lx, ly, budget_s):
+    """The float64 oracle (NumPy, as it stands) on the host cores: every core
+    available to the process steps its own column slab of the workload in a
+    spawned worker, and one worker alone on one core for comparison."""
+    cores = len(os.sched_getaffinity(0))
+    width = max(8, lx // cores)
+    # size the steps so that one worker's share takes about budget_s / 2
+    probe, dt = _oracle_throughput(lx, ly, 1, 32, 1, pin_one_core=True)
+    steps = int(max(1, min(20, budget_s / 2 / max(width * ly / (probe * 1e6), 1e-6))))
+    v_all, t_all = _oracle_throughput(lx, ly, cores, width, steps)
+    v_one, t_one = _oracle_throughput(lx, ly, 1, width, steps, pin_one_core=True)
+    return {"value": v_all, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} spawned workers, each {steps} steps of its own {width}x{ly} column slab "
+                      f"of the 2048x4096 RT lattice (periodic in x), NumPy float64, one thread each; "
+                      f"{t_all:.1f} s",
+            "one_core": {"value": v_one, "unit": "MLUPS", "cores": 1,
+                         "sample": f"one worker pinned to one core, {steps} steps of a {width}x{ly} slab; "
+                                   f"{t_one:.1f} s"},
+            "scaling_all_over_one": v_all / v_one}
 
 
 FP32_ARITHS = ("split", "fp64_terms", "fp64_collide")
@@ -438,37 +473,24 @@ def workload_config(lx, ly, world):
 
 
 def run_reference(args):
+    """The oracle arm: the float64 oracle on the host cores (every available
+    core steps its own column slab), one line with impl = reference."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cb = cpu_baseline(args.lx, args.ly, max(2.0, args.cpu_seconds / 3))
-    # each reference "step" is a bounded oracle sample of the same workload
-    import numpy as np
-
-    import synth
-    from oracle import model as M
-    rho, ux, uy, T, tt, tb = synth.rt_fields(args.lx, args.ly, 32, 0)
-    width = 32
-    p = M.Params(width, args.ly, tau=0.6, g=1e-5, t_top=tt, t_bottom=tb)
-    f = M.init_state(rho[:, :width], ux[:, :width], uy[:, :width], T[:, :width])
-    for _ in range(min(args.warmup, 3)):
-        f = M.step(f, p)
-    t0 = time.perf_counter()
-    c0 = time.process_time()
-    for _ in range(args.steps):
-        f = M.step(f, p)
-    dt = time.perf_counter() - t0
-    cores = round((time.process_time() - c0) / dt, 2)
-    v = width * args.ly * args.steps / dt / 1e6
+    cores = len(os.sched_getaffinity(0))
+    width = max(8, args.lx // cores)
+    _oracle_throughput(args.lx, args.ly, cores, width, max(1, min(args.warmup, 3)))  # warm-up
+    v, dt = _oracle_throughput(args.lx, args.ly, cores, width, args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.lx, args.ly, args.gpus),
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                             "cores_available": len(os.sched_getaffinity(0)),
-                             "sample": f"{width}x{args.ly} column slab of the RT lattice per step, NumPy float64"},
-            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "cpu_baseline_calibration": cb}
+                             "sample": f"per step: {cores} spawned workers, each one step of its own "
+                                       f"{width}x{args.ly} column slab of the RT lattice, NumPy float64, "
+                                       f"one thread each"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -505,6 +527,9 @@ def main():
     rc = lib.lbm_probe_fma(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 4096, 0,
                            ctypes.byref(tf), ctypes.byref(ms))
     fp64_peak = tf.value if rc == 0 else None
+    # the same peak from unit counts and the clock: SMs x 2 FP64 FMAs per
+    # clock x 2 flops x the SM clock sampled under load (max clock if none)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     clocks = None
     if "fp64" in only:
@@ -718,18 +743,25 @@ def main():
         res["gpu_launches"] = K
         res["finite_after_timed_steps"] = f64["finite"]
         peak = fp64_peak if fp64_peak else FP64_NOMINAL_TFLOPS
+        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak_units = {"sms": sms, "fp64_fma_per_clk_per_sm": 2, "sm_mhz": mhz,
+                      "tflops": sms * 2 * 2 * mhz * 1e6 / 1e12}
         achieved = FP64_FLOP_PER_SITE * sites / t_launch / 1e12
         res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak,
                            "traffic": FP64_TRAFFIC_BYTES_PER_SITE_NCU * sites,
-                           "traffic_source": "ncu 2048x1024 capture scaled by sites "
-                                             "(profiles/step_kernel_fp64_2048x1024.md)",
+                           "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                             "2048x1024 launch, scaled by sites",
                            "peak_source": ("measured FP64 FMA probe (lbm_probe_fma), this run" if fp64_peak
                                            else "nominal 1.25 TFLOP/s"),
                            "flop_per_site": FP64_FLOP_PER_SITE,
                            "flop_per_site_on_integer_pipe": FP64_FLOP_PER_SITE_MOMENT_SUMS,
                            "fp64_instr_per_site_ncu": FP64_INSTR_PER_SITE_NCU,
                            "fp64_issue_frac": FP64_INSTR_PER_SITE_NCU * sites / t_launch / (peak * 1e12 / 2),
+                           "fp64_pipe_only_frac": (FP64_FLOP_PER_SITE - FP64_FLOP_PER_SITE_MOMENT_SUMS) * sites
+                                                  / t_launch / 1e12 / peak,
+                           "fp64_pipe_flop_per_site_ncu": FP64_PIPE_FLOP_PER_SITE_NCU,
+                           "peak_from_units": peak_units,
                            "algorithmic_bytes_per_launch": BYTES_PER_SITE_FP64 * sites,
                            "hbm_gbs": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9,
                            "hbm_frac_of_measured": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9 / HBM_GBS_MEASURED}

@@ -250,8 +250,11 @@ int lbm_adjoint_step(lbm_ctx* ctx, const void* f_t, const double* lam_in,
  * host application whose device memory is all handed out by another allocator
  * (for example a framework's caching allocator that reserved the GPU up
  * front), and code that must not allocate after its set-up phase because
- * cudaMalloc can synchronise the device.  This call computes what
- * lbm_adjoint_step computes for a context with parameters *p.
+ * cudaMalloc can synchronise the device.  Its result equals that of
+ * lbm_adjoint_step for a context with parameters *p up to rounding: this call
+ * sums the equilibrium's cotangents pair by pair in float64 for every
+ * precision, where the context call contracts w-weighted cotangent moments
+ * (LBM_FP64) or sums in double-float (LBM_FP64_DF, LBM_FP32_SHIFTED).
  *
  * Arguments: f_t, lam_in and lam_out as for lbm_adjoint_step (caller-owned
  * device buffers, must not alias); stream is a cudaStream_t (NULL = legacy
@@ -264,8 +267,15 @@ int lbm_adjoint_step(lbm_ctx* ctx, const void* f_t, const double* lam_in,
  * holds this array until the process exits.  The halo rows of lam_out are
  * left untouched.
  *
- * Set-up: the first call on a device looks up the array's device address,
- * with that device current; make that first call before any stream capture.
+ * Set-up: every call looks up the array's device address on the current
+ * device (a host-side lookup, no device work), so the address stays right
+ * after a device reset.  The first call on a device also loads the library's
+ * device code there; make that first call before any stream capture.
+ *
+ * Errors: an error that earlier, unrelated calls left in the CUDA runtime's
+ * last-error state is cleared before the launches, so LBM_ERR_CUDA reports
+ * this call's own launch failures (and errors that the device context keeps
+ * for every call).
  *
  * Sharing: every call shares the array, and the array keeps the last call's
  * contents.  Each call overwrites every entry it reads, so nothing needs

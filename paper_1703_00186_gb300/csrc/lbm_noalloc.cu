@@ -8,8 +8,6 @@
 // below, which every GPU that loads the library holds until the process ends.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "lbm_adjoint_math.cuh"
 #include "lbm_device.cuh"
 
@@ -20,30 +18,20 @@ size_t element_size(int precision);
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 // Partial wall sums [wall (0 bottom, 1 top)][row offset from the wall 0..2][x].
 // Every call writes each slot it later reads, so nothing needs clearing.
 static __device__ __align__(256) double g_wall_partials[2 * 3 * LBM_NOALLOC_MAX_LX];
 
-std::mutex g_addr_mu;
-double* g_addr[kMaxDevices] = {};
-
-// Device address of g_wall_partials on the current device (looked up once per
-// device; host code cannot take the array's address directly).
+// Device address of g_wall_partials on the current device.  Host code cannot
+// take the array's address directly (its name there is a host-side stand-in),
+// so every call looks it up: a host-side lookup once the library's device
+// code is loaded on the device.  Not caching it keeps the address right after
+// a device reset, which reloads the device code, possibly elsewhere.
 cudaError_t wall_partials_ptr(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_wall_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_wall_partials);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -170,6 +158,9 @@ extern "C" int lbm_adjoint_step_noalloc(const lbm_params* p, const void* f_t, co
     return LBM_ERR_INVALID;
   double* partials = nullptr;
   if (wall_partials_ptr(&partials) != cudaSuccess) return LBM_ERR_CUDA;
+  // clear an error that earlier, unrelated calls left in the runtime's
+  // last-error state, so that the checks below see this call's launches only
+  (void)cudaGetLastError();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const dim3 grid((unsigned)((a.lx + 31) / 32), (unsigned)((a.ly + 3) / 4)), block(32, 4);
   if (p->precision != LBM_FP32_SHIFTED)

@@ -59,6 +59,21 @@ __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel
   T f[NPOP];
   if (fast_site(a, x)) pull_fast(src, site_off(a, y, x), a, f);
   else pull(src, x, y, a, f);
+  if constexpr (PREC == LBM_FP32_SHIFTED && F32M == FP32_ARITH_F64_COLLIDE) {
+    if (COLLIDE) {
+      // the float64 step on the decoded populations, walls included, stored
+      // back once: the error of the float32 storage alone
+      double g[NPOP];
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) g[l] = codec(l, f[l]);
+      walls(src, x, y, a, g, codec, [](int, double v) { return v; });
+      collide_fp64(g, a);
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) f[l] = codec.enc(l, g[l]);
+      store_site(dst, x, y, a, f);
+      return;
+    }
+  }
   walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
   if constexpr (PREC == LBM_FP64 && DFARITH) {
     if (COLLIDE) {
@@ -79,13 +94,6 @@ __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel
       collide_fp64(f, a);
     } else if constexpr (F32M == FP32_ARITH_F64_TERMS) {
       collide_fp32_f64terms(f, a);
-    } else if constexpr (F32M == FP32_ARITH_F64_COLLIDE) {
-      double g[NPOP];
-#pragma unroll
-      for (int l = 0; l < NPOP; ++l) g[l] = codec(l, f[l]);
-      collide_fp64(g, a);
-#pragma unroll
-      for (int l = 0; l < NPOP; ++l) f[l] = codec.enc(l, g[l]);
     } else {
       collide_fp32(f, a);
     }

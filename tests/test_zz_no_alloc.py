@@ -11,8 +11,11 @@ scratch is a fixed array inside the library.
 This test calls that entry point through the C ABI twice in a row, with
 different cotangents.  It checks each result against the context entry point
 lbm_adjoint_step on the same inputs, within the adjoint tolerance (1e-12 of
-each population plane's largest value).  It also checks that lam_out's halo
-rows stay untouched and that a lattice wider than the array is refused.
+each population plane's largest value), for every precision, for a lattice
+wider than one block of the wall kernel and for a periodic-y lattice (no
+walls, so the fixed array is not used).  It checks one call directly against
+the oracle's adjoint step, that lam_out's halo rows stay untouched, and that a
+lattice wider than the array is refused with nothing written.
 """
 import ctypes
 
@@ -28,15 +31,17 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_adjoint_matches_context_adjoint_on_two_calls(precision):
+@pytest.mark.parametrize("precision,lx,ly,periodic_y", [
+    ("fp64", 70, 37, False), ("fp32", 70, 37, False), ("fp64df", 70, 37, False),
+    ("fp64", 300, 12, False), ("fp64", 40, 24, True)])
+def test_noalloc_adjoint_matches_context_adjoint_on_two_calls(precision, lx, ly, periodic_y):
     from paper_1703_00186_gb300 import _lib as L
     from paper_1703_00186_gb300.lbm import Lattice
 
     lib = L.load()
-    lx, ly = 70, 37
     rho, ux, uy, T = synth.random_fields(lx, ly, 90, umax=0.08)
-    lat = Lattice(lx, ly, tau=0.7, g=1e-3, t_top=0.85, t_bottom=1.2, precision=precision, rho0=1.0)
+    lat = Lattice(lx, ly, tau=0.7, g=1e-3, t_top=0.85, t_bottom=1.2, precision=precision, rho0=1.0,
+                  periodic_y=periodic_y)
     lat.init(rho, ux, uy, T).step(3)
     f_t = lat.state().clone()
     gen = torch.Generator(device="cuda").manual_seed(91)
@@ -54,11 +59,46 @@ def test_noalloc_adjoint_matches_context_adjoint_on_two_calls(precision):
         assert torch.isnan(got[:, :3]).all() and torch.isnan(got[:, -3:]).all()
 
 
+def test_noalloc_adjoint_matches_the_oracle_adjoint():
+    import numpy as np
+
+    from oracle import adjoint as A, model as M
+    from paper_1703_00186_gb300 import _lib as L
+    from paper_1703_00186_gb300.lbm import Lattice
+
+    lib = L.load()
+    lx, ly = 20, 12
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.85, t_bottom=1.2)
+    rho, ux, uy, T = synth.random_fields(lx, ly, 92, umax=0.08)
+    f = M.run(M.init_state(rho, ux, uy, T), p, 2)
+    lam = np.random.default_rng(93).standard_normal(f.shape)
+    want = M.physical(A.adjoint_step(f, lam, p))
+    lat = Lattice(lx, ly, tau=p.tau, g=p.g, t_top=p.t_top, t_bottom=p.t_bottom)
+    f_t = torch.as_tensor(f, device="cuda")
+    lam_in = torch.as_tensor(lam, device="cuda")
+    got = torch.full(lat.shape, float("nan"), dtype=torch.float64, device="cuda")
+    rc = lib.lbm_adjoint_step_noalloc(ctypes.byref(lat.params), _ptr(f_t), _ptr(lam_in), _ptr(got),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == L.LBM_OK
+    g = M.physical(got.cpu().numpy())
+    err = (np.abs(g - want).max(axis=(1, 2)) / np.abs(want).max(axis=(1, 2))).max()
+    assert err <= 1e-12, err
+
+
 def test_noalloc_adjoint_refuses_lattices_wider_than_its_array():
+    # Buffers of the right size for the refused lattice, so that even a
+    # launch would stay inside them; the call must write nothing.
     from paper_1703_00186_gb300 import _lib as L
 
     lib = L.load()
-    big = L.LbmParams(L.LBM_NOALLOC_MAX_LX + 1, 8, L.LBM_FP64, 0, 0.8, 0.0, 1.0, 1.0, 1.0)
-    rc = lib.lbm_adjoint_step_noalloc(ctypes.byref(big), ctypes.c_void_p(256), ctypes.c_void_p(512),
-                                      ctypes.c_void_p(1024), None)
+    lx, ly = L.LBM_NOALLOC_MAX_LX + 1, 8
+    big = L.LbmParams(lx, ly, L.LBM_FP64, 0, 0.8, 0.0, 1.0, 1.0, 1.0)
+    shape = (37, ly + 6, lx)
+    f_t = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    lam_in = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    lam_out = torch.full(shape, 7.0, dtype=torch.float64, device="cuda")
+    rc = lib.lbm_adjoint_step_noalloc(ctypes.byref(big), _ptr(f_t), _ptr(lam_in), _ptr(lam_out),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == L.LBM_ERR_SIZE
+    torch.cuda.synchronize()
+    assert bool((lam_out == 7.0).all())
