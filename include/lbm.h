@@ -180,8 +180,35 @@ int lbm_step(lbm_ctx* ctx, int n);
  * current state untouched.  Used to recompute checkpointed trajectories. */
 int lbm_step_from(lbm_ctx* ctx, const void* src, void* dst);
 
+/* x-slab decomposition (Sect. 4: the lattice split along x over devices in a
+ * ring, each sub-lattice surrounded by three halo columns that the pbc step
+ * refills from the neighbours' adjoining physical columns; bulk sites, which
+ * read no halo column, overlap that exchange, Fig. "schedulingop").  A slab
+ * of w physical columns is a lattice of lx = w + 6 columns: columns 0..2 and
+ * w+3..w+5 are the halos, w+3 <= lx.
+ *
+ * lbm_step_columns: one time step from state src into state dst for the
+ *   sites of columns x0 <= x < x1 only (every physical row); the other
+ *   columns of dst are not written.  Column x pulls from columns x-3 .. x+3
+ *   (periodic in lx), so a slab's physical columns 3 <= x < w+3 read only
+ *   the slab and its halos.  0 <= x0 <= x1 <= lx; src and dst must not alias.
+ * lbm_pack_columns: copy columns x0 .. x0+n-1 of every population's physical
+ *   rows of state f into the contiguous buffer buf[37][ly][n] (element type of
+ *   the context's precision), for a send.
+ * lbm_unpack_columns: the inverse, from buf into those columns of f.
+ *   0 <= x0, 0 <= n, x0 + n <= lx.  Device buffers; asynchronous on the
+ *   context's stream. */
+int lbm_step_columns(lbm_ctx* ctx, const void* src, void* dst, int x0, int x1);
+int lbm_pack_columns(lbm_ctx* ctx, const void* f, int x0, int n, void* buf);
+int lbm_unpack_columns(lbm_ctx* ctx, const void* buf, int x0, int n, void* f);
+
 /* Device pointer of the buffer holding the current state. */
 void* lbm_current(const lbm_ctx* ctx);
+
+/* Make the context's other buffer the current state (no device work): after
+ * a step written into it piecewise with lbm_step_columns, as lbm_step does
+ * after each step. */
+int lbm_swap(lbm_ctx* ctx);
 
 /* Which kernel lbm_step runs for this context: LBM_PATH_TMA when the
  * LBM_FP32_SHIFTED step stages its pull sources with TMA loads (requested

@@ -63,6 +63,10 @@ SIGNATURES = {
     "lbm_step": (c_int, [c_void_p, c_int]),
     "lbm_step_from": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_current": (c_void_p, [c_void_p]),
+    "lbm_swap": (c_int, [c_void_p]),
+    "lbm_step_columns": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int]),
+    "lbm_pack_columns": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "lbm_unpack_columns": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "lbm_step_path": (c_int, [c_void_p]),
     "lbm_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_profiles": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -23,6 +23,10 @@ cudaError_t launch_finite(int prec, const void* src, const LatticeArgs& a, unsig
 cudaError_t launch_profiles(int prec, const void* src, double* out, const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_step_observe(const void* src, void* dst, const LatticeArgs& a, double* obs, cudaStream_t s);
 bool step_uses_tma(const LatticeArgs& a, const void* src);
+cudaError_t launch_step_columns(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a, int x0,
+                                int x1, cudaStream_t s);
+cudaError_t launch_columns_copy(int prec, bool pack, const void* from, void* to, const LatticeArgs& a, int x0, int n,
+                                cudaStream_t s);
 cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, double* lam_out,
                            const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux,
@@ -329,7 +333,37 @@ int lbm_step_from(lbm_ctx* c, const void* src, void* dst) {
   return cuda_check(c, launch_step(c->p.precision, true, src, dst, c->args, c->stream), "lbm_step_from");
 }
 
+int lbm_step_columns(lbm_ctx* c, const void* src, void* dst, int x0, int x1) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!src || !dst || src == dst) return fail(c, LBM_ERR_INVALID, "lbm_step_columns: bad buffers");
+  if (x0 < 0 || x1 < x0 || x1 > c->p.lx) return fail(c, LBM_ERR_INVALID, "lbm_step_columns: bad column range");
+  return cuda_check(c, launch_step_columns(c->p.precision, true, src, dst, c->args, x0, x1, c->stream),
+                    "lbm_step_columns");
+}
+
+int lbm_pack_columns(lbm_ctx* c, const void* f, int x0, int n, void* buf) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!f || !buf) return fail(c, LBM_ERR_INVALID, "lbm_pack_columns: NULL buffer");
+  if (x0 < 0 || n < 0 || x0 + n > c->p.lx) return fail(c, LBM_ERR_INVALID, "lbm_pack_columns: bad column range");
+  return cuda_check(c, launch_columns_copy(storage_prec(c->p.precision), true, f, buf, c->args, x0, n, c->stream),
+                    "lbm_pack_columns");
+}
+
+int lbm_unpack_columns(lbm_ctx* c, const void* buf, int x0, int n, void* f) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!f || !buf) return fail(c, LBM_ERR_INVALID, "lbm_unpack_columns: NULL buffer");
+  if (x0 < 0 || n < 0 || x0 + n > c->p.lx) return fail(c, LBM_ERR_INVALID, "lbm_unpack_columns: bad column range");
+  return cuda_check(c, launch_columns_copy(storage_prec(c->p.precision), false, buf, f, c->args, x0, n, c->stream),
+                    "lbm_unpack_columns");
+}
+
 void* lbm_current(const lbm_ctx* c) { return c ? c->buf[c->cur] : nullptr; }
+
+int lbm_swap(lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID;
+  c->cur ^= 1;
+  return LBM_OK;
+}
 
 int lbm_step_path(const lbm_ctx* c) {
   if (!c) return LBM_ERR_INVALID;

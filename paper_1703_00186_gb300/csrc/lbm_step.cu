@@ -48,11 +48,11 @@ struct Codec<LBM_FP32_SHIFTED> {
 // 2-3% from the same cap (60 bytes of spill, 4 -> 5 blocks per SM).
 template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, int F32M = FP32_ARITH_SPLIT>
 __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel(const void* __restrict__ src_,
-                                                       void* __restrict__ dst_, LatticeArgs a) {
+                                                       void* __restrict__ dst_, LatticeArgs a, int xb, int xe) {
   using T = typename Codec<PREC>::T;
-  const int x = blockIdx.x * BX + threadIdx.x;
+  const int x = xb + (int)blockIdx.x * BX + (int)threadIdx.x;  // columns xb <= x < xe
   const int y = blockIdx.y * BY + threadIdx.y;
-  if (x >= a.lx || y >= a.ly) return;
+  if (x >= xe || y >= a.ly) return;
   const T* __restrict__ src = static_cast<const T*>(src_);
   T* __restrict__ dst = static_cast<T*>(dst_);
   Codec<PREC> codec{&a};
@@ -443,34 +443,93 @@ static dim3 site_grid(const LatticeArgs& a) {
   return dim3((unsigned)((a.lx + BX - 1) / BX), (unsigned)((a.ly + BY - 1) / BY));
 }
 
-cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a,
-                        cudaStream_t s) {
-  const dim3 grid = site_grid(a), block(BX, BY);
+// One step (collide = false: propagate and bc only) from src to dst for the
+// sites of columns x0 <= x < x1 (every physical row); other columns of dst
+// are not written.
+cudaError_t launch_step_columns(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a, int x0,
+                                int x1, cudaStream_t s) {
+  if (x1 <= x0) return cudaSuccess;
+  const dim3 grid((unsigned)((x1 - x0 + BX - 1) / BX), (unsigned)((a.ly + BY - 1) / BY)), block(BX, BY);
   if (prec == LBM_FP64_DF) {
     if (collide)
-      step_kernel<LBM_FP64, true, true><<<grid, block, 0, s>>>(src, dst, a);
+      step_kernel<LBM_FP64, true, true><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
     else
-      step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a);
+      step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
   } else if (prec == LBM_FP64) {
     if (collide && a.regularized)
-      step_kernel<LBM_FP64, true, false, true><<<grid, block, 0, s>>>(src, dst, a);
+      step_kernel<LBM_FP64, true, false, true><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
     else if (collide)
-      step_kernel<LBM_FP64, true><<<grid, block, 0, s>>>(src, dst, a);
+      step_kernel<LBM_FP64, true><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
     else
-      step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a);
+      step_kernel<LBM_FP64, false><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
   } else {
-    if (collide && a.fp32_arith == FP32_ARITH_F64_TERMS) {
-      step_kernel<LBM_FP32_SHIFTED, true, false, false, FP32_ARITH_F64_TERMS><<<grid, block, 0, s>>>(src, dst, a);
-    } else if (collide && a.fp32_arith == FP32_ARITH_F64_COLLIDE) {
-      step_kernel<LBM_FP32_SHIFTED, true, false, false, FP32_ARITH_F64_COLLIDE><<<grid, block, 0, s>>>(src, dst, a);
-    } else if (collide) {
-      const cudaError_t e = launch_step_tma(src, dst, a, s);
-      if (e != cudaErrorNotSupported) return e;
-      (void)cudaGetLastError();  // a refused set-up call leaves no error behind
-      step_kernel<LBM_FP32_SHIFTED, true><<<grid, block, 0, s>>>(src, dst, a);
-    }
+    if (collide && a.fp32_arith == FP32_ARITH_F64_TERMS)
+      step_kernel<LBM_FP32_SHIFTED, true, false, false, FP32_ARITH_F64_TERMS><<<grid, block, 0, s>>>(src, dst, a, x0,
+                                                                                                    x1);
+    else if (collide && a.fp32_arith == FP32_ARITH_F64_COLLIDE)
+      step_kernel<LBM_FP32_SHIFTED, true, false, false, FP32_ARITH_F64_COLLIDE><<<grid, block, 0, s>>>(src, dst, a,
+                                                                                                      x0, x1);
+    else if (collide)
+      step_kernel<LBM_FP32_SHIFTED, true><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
     else
-      step_kernel<LBM_FP32_SHIFTED, false><<<grid, block, 0, s>>>(src, dst, a);
+      step_kernel<LBM_FP32_SHIFTED, false><<<grid, block, 0, s>>>(src, dst, a, x0, x1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int prec, bool collide, const void* src, void* dst, const LatticeArgs& a,
+                        cudaStream_t s) {
+  if (prec == LBM_FP32_SHIFTED && collide && a.fp32_arith == FP32_ARITH_SPLIT) {
+    const cudaError_t e = launch_step_tma(src, dst, a, s);
+    if (e != cudaErrorNotSupported) return e;
+    (void)cudaGetLastError();  // a refused set-up call leaves no error behind
+  }
+  return launch_step_columns(prec, collide, src, dst, a, 0, a.lx, s);
+}
+
+// Columns [x0, x0 + n) of every population's physical rows to / from a
+// contiguous buffer [37][ly][n] (the halo exchange of an x-slab, Sect. 4).
+template <typename T>
+__global__ void pack_columns_kernel(const T* __restrict__ f, T* __restrict__ buf, LatticeArgs a, int x0, int n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)NPOP * a.ly * n;
+  if (i >= total) return;
+  const int c = (int)(i % n);
+  const long long r = i / n;  // l * ly + y
+  const int l = (int)(r / a.ly), y = (int)(r - (long long)l * a.ly);
+  buf[i] = f[sidx(a, l, y, x0 + c)];
+}
+
+template <typename T>
+__global__ void unpack_columns_kernel(const T* __restrict__ buf, T* __restrict__ f, LatticeArgs a, int x0, int n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)NPOP * a.ly * n;
+  if (i >= total) return;
+  const int c = (int)(i % n);
+  const long long r = i / n;
+  const int l = (int)(r / a.ly), y = (int)(r - (long long)l * a.ly);
+  f[sidx(a, l, y, x0 + c)] = buf[i];
+}
+
+cudaError_t launch_columns_copy(int prec, bool pack, const void* from, void* to, const LatticeArgs& a, int x0, int n,
+                                cudaStream_t s) {
+  const long long total = (long long)NPOP * a.ly * n;
+  if (total == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (prec == LBM_FP32_SHIFTED) {
+    if (pack)
+      pack_columns_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(from), static_cast<float*>(to), a,
+                                                         x0, n);
+    else
+      unpack_columns_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(from), static_cast<float*>(to),
+                                                           a, x0, n);
+  } else {
+    if (pack)
+      pack_columns_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(from), static_cast<double*>(to),
+                                                          a, x0, n);
+    else
+      unpack_columns_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(from),
+                                                            static_cast<double*>(to), a, x0, n);
   }
   return cudaGetLastError();
 }

@@ -158,6 +158,38 @@ class Lattice:
         self._check(self.lib.lbm_step_from(self.ctx, _ptr(src), _ptr(dst)))
         return dst
 
+    def step_columns(self, src: torch.Tensor, dst: torch.Tensor, x0: int, x1: int):
+        """One step from src into dst for the sites of columns x0 <= x < x1."""
+        self._state(src, "src")
+        self._state(dst, "dst")
+        self._check(self.lib.lbm_step_columns(self.ctx, _ptr(src), _ptr(dst), int(x0), int(x1)))
+        return dst
+
+    def pack_columns(self, f: torch.Tensor, x0: int, n: int, buf: torch.Tensor):
+        """Columns x0 .. x0+n-1 of f's physical rows into buf (37, ly, n)."""
+        self._state(f, "f")
+        _check_tensor(buf, "buf", self.dtype, (NPOP, self.ly, n), self.device)
+        self._check(self.lib.lbm_pack_columns(self.ctx, _ptr(f), int(x0), int(n), _ptr(buf)))
+        return buf
+
+    def unpack_columns(self, buf: torch.Tensor, x0: int, n: int, f: torch.Tensor):
+        """buf (37, ly, n) into columns x0 .. x0+n-1 of f's physical rows."""
+        self._state(f, "f")
+        _check_tensor(buf, "buf", self.dtype, (NPOP, self.ly, n), self.device)
+        self._check(self.lib.lbm_unpack_columns(self.ctx, _ptr(buf), int(x0), int(n), _ptr(f)))
+        return f
+
+    def other(self) -> torch.Tensor:
+        """The buffer not holding the current state."""
+        cur = self.state()
+        return self.buffers[1] if cur is self.buffers[0] else self.buffers[0]
+
+    def swap(self):
+        """Make the other buffer current (after a step written into it with
+        step_columns): the role change lbm_step makes after each step."""
+        self._check(self.lib.lbm_swap(self.ctx))
+        return self
+
     def state(self) -> torch.Tensor:
         """The buffer holding the current state (a view; it changes role at each step)."""
         ptr = self.lib.lbm_current(self.ctx)
