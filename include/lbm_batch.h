@@ -11,7 +11,13 @@
  *    shared memory); nine tile shapes;
  *  - one launch of the single-lattice step kernel per lattice (its constants
  *    in the kernel parameters), the lattices spread over eight streams that
- *    the graph runs concurrently, each lattice's steps in order.
+ *    the graph runs concurrently, each lattice's steps in order;
+ *  - (LBM_FP32_SHIFTED batches whose lattices each hold fewer than 2^31
+ *    elements) one kernel launch per group of up to 64 lattices whose blocks
+ *    walk the group's tiles, with every lattice's constants in a table passed
+ *    as the kernel's parameters (no shared-memory staging); three tile
+ *    shapes.  For other batches these candidates run the shared-memory tile
+ *    kernel of the same shape.
  * lbm_batch_autotune times every candidate on the batch itself and keeps the
  * fastest.  The paper has no batched mode; the per-lattice step is the one of
  * include/lbm.h (same readings, layout and population order).  The
@@ -51,15 +57,18 @@ typedef struct lbm_lattice_desc {
 typedef struct lbm_batch lbm_batch;
 
 /* Number of launch candidates lbm_batch_autotune chooses from (the nine tile
- * shapes of the one-launch batch kernel, then the per-lattice launches), the
- * block shape of candidate `i` (threads along x and y), its sites per thread
- * along y (a tile covers bx x (by * rows) sites), and whether it launches
- * the single-lattice kernel once per lattice (1) or is a tile shape (0).
+ * shapes of the shared-memory tile kernel, then the per-lattice launches,
+ * then the three tile shapes of the parameter-table kernel), the block shape
+ * of candidate `i` (threads along x and y), its sites per thread along y (a
+ * tile covers bx x (by * rows) sites), whether it launches the single-lattice
+ * kernel once per lattice (1) or not (0), and its kind (LBM_BATCH_*).
  * LBM_ERR_INVALID for a bad i. */
+enum { LBM_BATCH_SHARED_TILES = 0, LBM_BATCH_PER_LATTICE = 1, LBM_BATCH_PARAM_TILES = 2 };
 int lbm_batch_tile_count(void);
 int lbm_batch_tile_shape(int i, int* bx, int* by);
 int lbm_batch_tile_rows(int i);
 int lbm_batch_tile_per_lattice(int i);
+int lbm_batch_tile_kind(int i);
 
 /* Create a batch of n >= 1 lattices in `precision` (LBM_FP64 or
  * LBM_FP32_SHIFTED).  descs is a host array of n entries.  stream: cudaStream_t. */

@@ -31,6 +31,9 @@ LBM_PATH_PLAIN = 0
 LBM_PATH_TMA = 1
 LBM_NOALLOC_MAX_LX = 16384
 LBM_NOBS = 8
+LBM_BATCH_SHARED_TILES = 0
+LBM_BATCH_PER_LATTICE = 1
+LBM_BATCH_PARAM_TILES = 2
 
 c_int = ctypes.c_int
 c_double = ctypes.c_double
@@ -85,6 +88,7 @@ SIGNATURES = {
     "lbm_probe_fma": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
     "lbm_batch_tile_count": (c_int, []),
     "lbm_batch_tile_per_lattice": (c_int, [c_int]),
+    "lbm_batch_tile_kind": (c_int, [c_int]),
     "lbm_batch_tile_shape": (c_int, [c_int, P(c_int), P(c_int)]),
     "lbm_batch_tile_rows": (c_int, [c_int]),
     "lbm_batch_create": (c_int, [P(c_void_p), c_int, P(LbmLatticeDesc), c_int, c_void_p]),

@@ -89,11 +89,20 @@ class Batch:
 
     @staticmethod
     def tile_labels():
-        """A name for every launch candidate ("32x4x8" for a tile shape,
-        "per-lattice 32x4" for the per-lattice launches)."""
+        """A name for every launch candidate ("32x4x8" for a shared-memory tile
+        shape, "per-lattice 32x4" for the per-lattice launches, "params
+        32x4x8" for a tile shape of the parameter-table kernel)."""
         lib = L.load()
-        return [f"per-lattice {bx}x{by}" if lib.lbm_batch_tile_per_lattice(i) == 1 else f"{bx}x{by}x{rows}"
-                for i, (bx, by, rows) in enumerate(Batch.tile_shapes())]
+        out = []
+        for i, (bx, by, rows) in enumerate(Batch.tile_shapes()):
+            kind = lib.lbm_batch_tile_kind(i)
+            if kind == L.LBM_BATCH_PER_LATTICE:
+                out.append(f"per-lattice {bx}x{by}")
+            elif kind == L.LBM_BATCH_PARAM_TILES:
+                out.append(f"params {bx}x{by}x{rows}")
+            else:
+                out.append(f"{bx}x{by}x{rows}")
+        return out
 
     def set_tile(self, t: int):
         self._check(self.lib.lbm_batch_set_tile(self.h, int(t)))

@@ -48,7 +48,13 @@ constexpr int kTileRows[kTiles] = {1, 1, 1, 1, 1, 1, 2, 4, 8};
 // single-lattice kernel (its constants in the kernel parameters, 32 x 4
 // blocks), the lattices spread over kAux streams, all captured in one graph.
 constexpr int kPerLattice = kTiles;
-constexpr int kCandidates = kTiles + 1;
+// Candidates kTiles + 1 .. : FP32-store tiles with the per-lattice constants
+// in the kernel parameters (batch_param_kernel), 32 x 4 threads, these rows
+// per thread.
+constexpr int kParamTiles = 3;
+constexpr int kParamRows[kParamTiles] = {1, 4, 8};
+constexpr int kParamFirst = kTiles + 1;
+constexpr int kCandidates = kParamFirst + kParamTiles;
 constexpr int kAux = 8;
 
 template <int PREC>
@@ -67,6 +73,8 @@ struct BCodec<LBM_FP32_SHIFTED> {
   __device__ double operator()(int l, float v) const { return a->w_rho0[l] + (double)v; }
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
+
+using Codec32 = BCodec<LBM_FP32_SHIFTED>;
 
 // One tile of the batch work list; block-wide: every thread of the block
 // calls it (threads outside the lattice skip the work but reach the barriers).
@@ -130,6 +138,100 @@ __global__ void __launch_bounds__(TBX * TBY, PREC == LBM_FP32_SHIFTED ? 4 * 128 
   __shared__ const void* s_src;
   __shared__ void* s_dst;
   batch_tile<PREC, TBX, TBY, DFARITH, false, ROWS>(ent, tile_start, tile_lattice, parity, blockIdx.x, sa, s_src, s_dst);
+}
+
+// ---------------------------------------------------------------------------
+// FP32-store tiles with the per-lattice constants in the kernel parameters.
+//
+// The shared-memory tile kernel above copies each tile's LatticeArgs into
+// shared memory and reads every constant back from there (38 shared loads
+// per site, and the registers that hold them).  This kernel takes a table of
+// up to kParamLattices lattices as a __grid_constant__ parameter instead: a
+// block finds its lattice by a binary search over the table's tile offsets
+// (block-uniform, in the parameter bank), and every per-lattice constant it
+// then reads - the pull and store offsets, the size, the density, tau and g
+// terms of the collide - is a load from the parameter bank at a block-uniform
+// address, as in the single-lattice kernel, where these are compile-time
+// parameter offsets.  The quadrature constants, the same for every lattice,
+// come from one LatticeArgs parameter.  Wall rows and the three columns next
+// to the periodic seam read the full LatticeArgs of their lattice from global
+// memory (the wall ratios, the shift constants and the general index path).
+// Batches of more lattices run one launch per group of kParamLattices.
+constexpr int kParamLattices = 64;
+
+struct ParamLat {
+  long long tile_start;     // first tile of the lattice in the group's work list
+  const void* f[2];         // ping-pong state buffers
+  const LatticeArgs* args;  // the lattice's full constants (device copy)
+  int lx, ly, tiles_x, pad;
+  float omega_f, omc_f, df_rho0[2], df_e0[2], df_tshift[2], df_taug_r[2], df_g_r[2];
+  int pull_off[NPOP];   // bytes, as LatticeArgs::pull_off (32-bit lattices only)
+  int plane_off[NPOP];  // bytes, as LatticeArgs::plane_off
+};
+
+struct ParamTable {
+  int n, pad;
+  ParamLat e[kParamLattices];
+};
+static_assert(sizeof(ParamTable) + sizeof(LatticeArgs) + 16 <= 32764, "kernel parameters above 32 KB");
+
+template <int TBX, int TBY, int ROWS>
+__global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
+    batch_param_kernel(const __grid_constant__ ParamTable t, const __grid_constant__ LatticeArgs m, int parity) {
+  const long long b = blockIdx.x;
+  int lo = 0, hi = t.n - 1;  // the last lattice whose first tile is <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.e[mid].tile_start <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const ParamLat& e = t.e[lo];
+  F32Args a;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    a.df_rho0[k] = e.df_rho0[k];
+    a.df_e0[k] = e.df_e0[k];
+    a.df_tshift[k] = e.df_tshift[k];
+    a.df_taug_r[k] = e.df_taug_r[k];
+    a.df_g_r[k] = e.df_g_r[k];
+    a.df_half_r2[k] = m.df_half_r2[k];
+    a.df_r2[k] = m.df_r2[k];
+  }
+  a.omega_f = e.omega_f;
+  a.omc_f = e.omc_f;
+#pragma unroll
+  for (int j = 0; j < NSHELL; ++j) {
+    a.w_shell_f[j] = m.w_shell_f[j];
+    a.c2_shell_f[j] = m.c2_shell_f[j];
+  }
+  const int lx = e.lx, ly = e.ly;
+  const long long tl = b - e.tile_start;
+  const int ty = (int)(tl / e.tiles_x), tx = (int)(tl - (long long)ty * e.tiles_x);
+  const int x = tx * TBX + threadIdx.x;
+  const float* __restrict__ src = static_cast<const float*>(e.f[parity]);
+  float* __restrict__ dst = static_cast<float*>(const_cast<void*>(e.f[parity ^ 1]));
+#pragma unroll 1
+  for (int r = 0; r < ROWS; ++r) {
+    const int y = (ty * ROWS + r) * TBY + threadIdx.y;
+    if (x < lx && y < ly) {
+      float f[NPOP];
+      const int site = (y + HALO) * lx + x;
+      if (y >= 3 && y < ly - 3 && x >= 3 && x < lx - 3) {
+        const char* s = reinterpret_cast<const char*>(src + site);
+#pragma unroll
+        for (int l = 0; l < NPOP; ++l) f[l] = __ldg(reinterpret_cast<const float*>(s + e.pull_off[l]));
+      } else {
+        const LatticeArgs& ga = *e.args;
+        Codec32 codec{&ga};
+        pull(src, x, y, ga, f);
+        walls(src, x, y, ga, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+      }
+      collide_fp32(f, a);
+      char* d = reinterpret_cast<char*>(dst + site);
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) *reinterpret_cast<float*>(d + e.plane_off[l]) = f[l];
+    }
+  }
 }
 
 // Grid barrier of the persistent kernel with a bounded wait.  State in global
@@ -223,6 +325,19 @@ cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long lo
   return cudaGetLastError();
 }
 
+cudaError_t launch_param_tile(int i, const ParamTable& t, long long blocks, const LatticeArgs& m, int parity,
+                              cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)blocks), block(32, 4);
+  if (kParamRows[i] == 1)
+    batch_param_kernel<32, 4, 1><<<grid, block, 0, s>>>(t, m, parity);
+  else if (kParamRows[i] == 4)
+    batch_param_kernel<32, 4, 4><<<grid, block, 0, s>>>(t, m, parity);
+  else
+    batch_param_kernel<32, 4, 8><<<grid, block, 0, s>>>(t, m, parity);
+  return cudaGetLastError();
+}
+
 template <int PREC>
 cudaError_t launch_tile(int tile, long long blocks, const BatchEntry* ent, const long long* ts, const int* tl,
                         int parity, cudaStream_t s) {
@@ -263,6 +378,11 @@ struct lbm_batch {
   std::vector<int> order;  // lattices by decreasing size
   std::vector<int> lane;   // stream of each lattice (balanced by sites)
   GridBarrier* d_bar;  // persistent-kernel barrier state
+  // parameter-table candidates: usable for FP32-store batches whose lattices
+  // all have 32-bit offsets; one table and block count per group of lattices
+  bool param_ok;
+  std::vector<ParamTable> ptab[kParamTiles];
+  std::vector<long long> pblocks[kParamTiles];
   char err[512];
 };
 
@@ -283,8 +403,23 @@ int bcuda(lbm_batch* b, cudaError_t e, const char* what) {
   return bfail(b, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// The shared-memory tile shape with the same threads and rows as parameter
+// candidate i (used where the parameter tables do not apply).
+constexpr int param_fallback(int i) { return kParamRows[i] == 1 ? 0 : kParamRows[i] == 4 ? 7 : 8; }
+
 cudaError_t launch_batch(const lbm_batch* b, int parity, cudaStream_t s) {
-  const int t = b->tile;
+  int t = b->tile;
+  if (t >= kParamFirst) {
+    const int i = t - kParamFirst;
+    if (b->param_ok) {
+      for (size_t g = 0; g < b->ptab[i].size(); ++g) {
+        const cudaError_t e = launch_param_tile(i, b->ptab[i][g], b->pblocks[i][g], b->args[0], parity, s);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    t = param_fallback(i);
+  }
   if (b->precision == LBM_FP64_DF)
     return launch_tile<LBM_FP64_DF>(t, b->blocks[t], b->d_ent, b->d_tiles[t], b->d_tile_lat[t], parity, s);
   if (b->precision == LBM_FP64)
@@ -389,14 +524,19 @@ int lbm_batch_tile_count(void) { return kCandidates; }
 
 int lbm_batch_tile_shape(int i, int* bx, int* by) {
   if (i < 0 || i >= kCandidates || !bx || !by) return LBM_ERR_INVALID;
-  *bx = i == kPerLattice ? 32 : kTileBX[i];  // the single-lattice kernel's 32 x 4 blocks
-  *by = i == kPerLattice ? 4 : kTileBY[i];
+  *bx = i >= kPerLattice ? 32 : kTileBX[i];  // per-lattice and parameter candidates: 32 x 4 blocks
+  *by = i >= kPerLattice ? 4 : kTileBY[i];
   return LBM_OK;
 }
 
 int lbm_batch_tile_rows(int i) {
   if (i < 0 || i >= kCandidates) return LBM_ERR_INVALID;
-  return i == kPerLattice ? 1 : kTileRows[i];
+  return i == kPerLattice ? 1 : i >= kParamFirst ? kParamRows[i - kParamFirst] : kTileRows[i];
+}
+
+int lbm_batch_tile_kind(int i) {
+  if (i < 0 || i >= kCandidates) return LBM_ERR_INVALID;
+  return i == kPerLattice ? LBM_BATCH_PER_LATTICE : i >= kParamFirst ? LBM_BATCH_PARAM_TILES : LBM_BATCH_SHARED_TILES;
 }
 
 int lbm_batch_tile_per_lattice(int i) {
@@ -466,6 +606,48 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
       cudaGetLastError();
       free_batch(b);
       return LBM_ERR_CUDA;
+    }
+  }
+  // parameter tables (FP32-store, 32-bit offsets)
+  b->param_ok = precision == LBM_FP32_SHIFTED;
+  for (int i = 0; i < n; ++i) b->param_ok = b->param_ok && b->args[i].idx32;
+  if (b->param_ok) {
+    for (int t = 0; t < kParamTiles; ++t) {
+      for (int g0 = 0; g0 < n; g0 += kParamLattices) {
+        ParamTable tab;
+        std::memset(&tab, 0, sizeof tab);
+        tab.n = std::min(kParamLattices, n - g0);
+        long long start = 0;
+        for (int k = 0; k < tab.n; ++k) {
+          const int i = g0 + k;
+          const LatticeArgs& a = b->args[i];
+          ParamLat& e = tab.e[k];
+          const int rows = 4 * kParamRows[t];
+          e.tile_start = start;
+          e.tiles_x = (a.lx + 31) / 32;
+          start += (long long)e.tiles_x * ((a.ly + rows - 1) / rows);
+          e.f[0] = b->fa[i];
+          e.f[1] = b->fb[i];
+          e.args = &b->d_ent[i].a;
+          e.lx = a.lx;
+          e.ly = a.ly;
+          e.omega_f = a.omega_f;
+          e.omc_f = a.omc_f;
+          for (int c = 0; c < 2; ++c) {
+            e.df_rho0[c] = a.df_rho0[c];
+            e.df_e0[c] = a.df_e0[c];
+            e.df_tshift[c] = a.df_tshift[c];
+            e.df_taug_r[c] = a.df_taug_r[c];
+            e.df_g_r[c] = a.df_g_r[c];
+          }
+          for (int l = 0; l < NPOP; ++l) {
+            e.pull_off[l] = (int)a.pull_off[l];
+            e.plane_off[l] = (int)a.plane_off[l];
+          }
+        }
+        b->ptab[t].push_back(tab);
+        b->pblocks[t].push_back(start);
+      }
     }
   }
   if (cudaMalloc(&b->d_bar, sizeof(GridBarrier)) != cudaSuccess ||

@@ -444,8 +444,11 @@ __device__ __forceinline__ DF df_scale2(DF x, float p2) { return {x.hi * p2, x.l
 // collide conserves mass and energy and adds exactly rho g to the momentum.
 // PAIRED relaxes each (+, -) pair with one packed FMA (fewer issue slots, a few
 // more live registers); the results are identical either way.
-template <bool PAIRED = true>
-__device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs& a) {
+// A is LatticeArgs or any type with the same float32 / double-float members
+// (F32Args below), so that a batch kernel can pass per-lattice values held in
+// its kernel parameters.
+template <bool PAIRED = true, typename A = LatticeArgs>
+__device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const A& a) {
   MomentsDF dev;
   SplitSums dev_raw;
   float rf = 0.f;
@@ -528,6 +531,15 @@ __device__ __forceinline__ void collide_fp32(float (&d)[NPOP], const LatticeArgs
     }
   }
 }
+
+// The members of LatticeArgs that collide_fp32 reads, as plain values: the
+// per-lattice ones (rho0, tau and g) and the quadrature's float32 copies.
+struct F32Args {
+  float df_rho0[2], df_e0[2], df_tshift[2], df_taug_r[2], df_g_r[2];
+  float omega_f, omc_f;
+  float df_half_r2[2], df_r2[2];
+  float w_shell_f[NSHELL], c2_shell_f[NSHELL];
+};
 
 // Exact moment sums of the populations w_rho0[l] + d_l held as float32
 // deviations d_l: the deviations convert exactly to 96-bit fixed point from

@@ -58,13 +58,14 @@ def oracle_run(spec, f, n):
 
 def test_tile_shapes():
     shapes = Batch.tile_shapes()
-    assert len(shapes) == 10
+    assert len(shapes) == 13
     assert all(bx * by <= 256 and rows >= 1 for bx, by, rows in shapes)
     labels = Batch.tile_labels()
-    assert labels[-1] == "per-lattice 32x4" and not any(lb.startswith("per") for lb in labels[:-1])
+    assert labels[9] == "per-lattice 32x4" and not any(lb.startswith("per") for i, lb in enumerate(labels) if i != 9)
+    assert labels[10:] == ["params 32x4x1", "params 32x4x4", "params 32x4x8"]
 
 
-@pytest.mark.parametrize("tile", range(10))
+@pytest.mark.parametrize("tile", range(13))
 def test_batch_fp64_matches_oracle_for_every_tile_shape(tile):
     specs, flds = build("fp64")
     b = Batch(specs, precision="fp64")
@@ -79,7 +80,7 @@ def test_batch_fp64_matches_oracle_for_every_tile_shape(tile):
     assert b.status() == 0
 
 
-@pytest.mark.parametrize("tile", [0, 9])
+@pytest.mark.parametrize("tile", [0, 9, 10, 11, 12])
 def test_batch_fp32_one_step_matches_oracle(tile):
     specs, flds = build("fp32")
     b = Batch(specs, precision="fp32")
@@ -192,3 +193,33 @@ def test_per_lattice_launches_match_the_batch_kernel(precision, tol):
             w = K["w"][:, None, None] * specs[i]["rho0"]
             sa, sb = sa + w, sb + w
         assert plane_err(sb, sa) <= tol, i
+
+
+@pytest.mark.parametrize("tile", [10, 12])
+def test_parameter_table_groups_match_per_lattice_launches(tile):
+    # 70 lattices: two launches per step (groups of 64 and 6 lattices), each
+    # lattice's constants read from the kernel-parameter table; against the
+    # single-lattice kernel launched per lattice, to rounding
+    rng = np.random.default_rng(5)
+    specs, flds = [], []
+    for i in range(70):
+        lx, ly = int(rng.integers(3, 40)), int(rng.integers(6, 30))
+        rho, ux, uy, T, tt, tb = synth.rt_fields(lx, ly, 2, 100 + i, delta=0.4, width=1.5)
+        specs.append(dict(lx=lx, ly=ly, tau=float(rng.uniform(0.6, 1.0)), g=float(rng.uniform(0, 1e-3)),
+                          t_top=tt, t_bottom=tb, rho0=float(rho.mean())))
+        flds.append((rho, ux, uy, T))
+    a = Batch(specs, precision="fp32")
+    b = Batch(specs, precision="fp32")
+    a.set_tile(9)
+    b.set_tile(tile)
+    for i, f in enumerate(flds):
+        a.init(i, *f)
+        b.init(i, *f)
+    a.step(3)
+    b.step(3)
+    assert a.status() == 0 and b.status() == 0
+    for i in range(len(specs)):
+        w = K["w"][:, None, None] * specs[i]["rho0"]
+        sa = a.state(i).cpu().numpy().astype(np.float64) + w
+        sb = b.state(i).cpu().numpy().astype(np.float64) + w
+        assert plane_err(sb, sa) <= 1e-6, i
