@@ -161,6 +161,7 @@ constexpr int kParamLattices = 64;
 
 struct ParamLat {
   long long tile_start;     // first tile of the lattice in the group's work list
+  long long edge_start;     // first edge site of the lattice in the group's edge list
   const void* f[2];         // ping-pong state buffers
   const LatticeArgs* args;  // the lattice's full constants (device copy)
   int lx, ly, tiles_x, pad;
@@ -216,15 +217,11 @@ __global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
     if (x < lx && y < ly) {
       float f[NPOP];
       const int site = (y + HALO) * lx + x;
-      if (y >= 3 && y < ly - 3 && x >= 3 && x < lx - 3) {
+      if (y < 3 || y >= ly - 3 || x < 3 || x >= lx - 3) continue;  // edge sites: batch_edge_kernel
+      {
         const char* s = reinterpret_cast<const char*>(src + site);
 #pragma unroll
         for (int l = 0; l < NPOP; ++l) f[l] = __ldg(reinterpret_cast<const float*>(s + e.pull_off[l]));
-      } else {
-        const LatticeArgs& ga = *e.args;
-        Codec32 codec{&ga};
-        pull(src, x, y, ga, f);
-        walls(src, x, y, ga, f, codec, [&](int l, double v) { return codec.enc(l, v); });
       }
       collide_fp32(f, a);
       char* d = reinterpret_cast<char*>(dst + site);
@@ -232,6 +229,58 @@ __global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
       for (int l = 0; l < NPOP; ++l) *reinterpret_cast<float*>(d + e.plane_off[l]) = f[l];
     }
   }
+}
+
+// Number of edge sites of a lattice: the three rows next to each wall, and
+// the three columns next to the periodic seam on each side in the rows
+// between (all columns where lx < 6).
+__host__ __device__ inline long long edge_sites(int lx, int ly) {
+  const int side_cols = lx < 6 ? lx : 6;
+  return 6LL * lx + (long long)side_cols * (ly - 6);
+}
+
+// The edge sites of every lattice of the group (those batch_param_kernel
+// leaves out): the walls and the seam columns, through the general index path
+// and the lattice's full LatticeArgs in global memory.  One thread per edge
+// site; a thread finds its lattice by binary search over the edge offsets.
+__global__ void __launch_bounds__(128) batch_edge_kernel(const __grid_constant__ ParamTable t,
+                                                         const __grid_constant__ LatticeArgs m, int parity,
+                                                         long long total) {
+  const long long j = blockIdx.x * 128LL + threadIdx.x;
+  if (j >= total) return;
+  int lo = 0, hi = t.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.e[mid].edge_start <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  const ParamLat& e = t.e[lo];
+  const int lx = e.lx, ly = e.ly;
+  long long k = j - e.edge_start;
+  int x, y;
+  if (k < 3LL * lx) {  // bottom rows
+    y = (int)(k / lx);
+    x = (int)(k - (long long)y * lx);
+  } else if ((k -= 3LL * lx) < 3LL * lx) {  // top rows
+    const int r = (int)(k / lx);
+    y = ly - 3 + r;
+    x = (int)(k - (long long)r * lx);
+  } else {  // seam columns of the rows in between
+    k -= 3LL * lx;
+    const int side_cols = lx < 6 ? lx : 6;
+    const int r = (int)(k / side_cols), c = (int)(k - (long long)r * side_cols);
+    y = 3 + r;
+    x = lx < 6 ? c : (c < 3 ? c : lx - 6 + c);
+  }
+  const LatticeArgs& ga = *e.args;
+  const float* __restrict__ src = static_cast<const float*>(e.f[parity]);
+  float* __restrict__ dst = static_cast<float*>(const_cast<void*>(e.f[parity ^ 1]));
+  Codec32 codec{&ga};
+  float f[NPOP];
+  pull(src, x, y, ga, f);
+  walls(src, x, y, ga, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+  collide_fp32(f, ga);
+  store_site(dst, x, y, ga, f);
 }
 
 // Grid barrier of the persistent kernel with a bounded wait.  State in global
@@ -325,8 +374,13 @@ cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_param_tile(int i, const ParamTable& t, long long blocks, const LatticeArgs& m, int parity,
-                              cudaStream_t s) {
+cudaError_t launch_param_tile(int i, const ParamTable& t, long long blocks, long long edges, const LatticeArgs& m,
+                              int parity, cudaStream_t s) {
+  if (edges > 0) {
+    batch_edge_kernel<<<(unsigned)((edges + 127) / 128), 128, 0, s>>>(t, m, parity, edges);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (blocks <= 0) return cudaSuccess;
   const dim3 grid((unsigned)blocks), block(32, 4);
   if (kParamRows[i] == 1)
@@ -383,6 +437,7 @@ struct lbm_batch {
   bool param_ok;
   std::vector<ParamTable> ptab[kParamTiles];
   std::vector<long long> pblocks[kParamTiles];
+  std::vector<long long> pedges[kParamTiles];
   char err[512];
 };
 
@@ -413,7 +468,8 @@ cudaError_t launch_batch(const lbm_batch* b, int parity, cudaStream_t s) {
     const int i = t - kParamFirst;
     if (b->param_ok) {
       for (size_t g = 0; g < b->ptab[i].size(); ++g) {
-        const cudaError_t e = launch_param_tile(i, b->ptab[i][g], b->pblocks[i][g], b->args[0], parity, s);
+        const cudaError_t e =
+            launch_param_tile(i, b->ptab[i][g], b->pblocks[i][g], b->pedges[i][g], b->args[0], parity, s);
         if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
@@ -617,13 +673,15 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
         ParamTable tab;
         std::memset(&tab, 0, sizeof tab);
         tab.n = std::min(kParamLattices, n - g0);
-        long long start = 0;
+        long long start = 0, edges = 0;
         for (int k = 0; k < tab.n; ++k) {
           const int i = g0 + k;
           const LatticeArgs& a = b->args[i];
           ParamLat& e = tab.e[k];
           const int rows = 4 * kParamRows[t];
           e.tile_start = start;
+          e.edge_start = edges;
+          edges += edge_sites(a.lx, a.ly);
           e.tiles_x = (a.lx + 31) / 32;
           start += (long long)e.tiles_x * ((a.ly + rows - 1) / rows);
           e.f[0] = b->fa[i];
@@ -647,6 +705,7 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
         }
         b->ptab[t].push_back(tab);
         b->pblocks[t].push_back(start);
+        b->pedges[t].push_back(edges);
       }
     }
   }
