@@ -217,11 +217,16 @@ __global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
     if (x < lx && y < ly) {
       float f[NPOP];
       const int site = (y + HALO) * lx + x;
-      if (y < 3 || y >= ly - 3 || x < 3 || x >= lx - 3) continue;  // edge sites: batch_edge_kernel
-      {
+      if (y < 3 || y >= ly - 3) continue;  // wall rows: batch_edge_kernel
+      if (x >= 3 && x < lx - 3) {
         const char* s = reinterpret_cast<const char*>(src + site);
 #pragma unroll
         for (int l = 0; l < NPOP; ++l) f[l] = __ldg(reinterpret_cast<const float*>(s + e.pull_off[l]));
+      } else {  // the three columns next to the periodic seam on each side
+        const char* s = reinterpret_cast<const char*>(src + (y + HALO) * lx);
+#pragma unroll
+        for (int l = 0; l < NPOP; ++l)
+          f[l] = __ldg(reinterpret_cast<const float*>(s + e.pull_off[l]) + (wrap_x(x - vx(l), lx) + vx(l)));
       }
       collide_fp32(f, a);
       char* d = reinterpret_cast<char*>(dst + site);
@@ -231,17 +236,12 @@ __global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
   }
 }
 
-// Number of edge sites of a lattice: the three rows next to each wall, and
-// the three columns next to the periodic seam on each side in the rows
-// between (all columns where lx < 6).
-__host__ __device__ inline long long edge_sites(int lx, int ly) {
-  const int side_cols = lx < 6 ? lx : 6;
-  return 6LL * lx + (long long)side_cols * (ly - 6);
-}
+// Number of edge sites of a lattice: the three rows next to each wall.
+__host__ __device__ inline long long edge_sites(int lx, int ly) { return 6LL * lx; }
 
 // The edge sites of every lattice of the group (those batch_param_kernel
-// leaves out): the walls and the seam columns, through the general index path
-// and the lattice's full LatticeArgs in global memory.  One thread per edge
+// leaves out): the three rows next to each wall, through the general index
+// path, the walls and the lattice's full LatticeArgs in global memory.  One thread per edge
 // site; a thread finds its lattice by binary search over the edge offsets.
 __global__ void __launch_bounds__(128) batch_edge_kernel(const __grid_constant__ ParamTable t,
                                                          const __grid_constant__ LatticeArgs m, int parity,
@@ -265,12 +265,8 @@ __global__ void __launch_bounds__(128) batch_edge_kernel(const __grid_constant__
     const int r = (int)(k / lx);
     y = ly - 3 + r;
     x = (int)(k - (long long)r * lx);
-  } else {  // seam columns of the rows in between
-    k -= 3LL * lx;
-    const int side_cols = lx < 6 ? lx : 6;
-    const int r = (int)(k / side_cols), c = (int)(k - (long long)r * side_cols);
-    y = 3 + r;
-    x = lx < 6 ? c : (c < 3 ? c : lx - 6 + c);
+  } else {
+    return;  // not reached: the edge list holds the wall rows only
   }
   const LatticeArgs& ga = *e.args;
   const float* __restrict__ src = static_cast<const float*>(e.f[parity]);
