@@ -147,15 +147,24 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const void* __res
   Dec<PREC> dec{&a};
   SiteFields sf;
   {
-    double f[NPOP];
-    {
-      S g[NPOP];
-      pull(src, x, y, a, g);
+    S g[NPOP];
+    pull(src, x, y, a, g);
+    Moments mo;
+    bool exact = false;
+    if constexpr (PREC == LBM_FP32_SHIFTED) {
+      // away from the walls the moment sums come straight from the float32
+      // bit patterns (exact, integer pipe): no float64 decode of the 37
+      // populations, which would take 74 FP64 issue slots
+      if (a.periodic_y || (y >= 3 && y < a.ly - 3)) exact = moment_sums_f32_exact(g, a, mo);
+    }
+    if (!exact) {
+      double f[NPOP];
 #pragma unroll
       for (int l = 0; l < NPOP; ++l) f[l] = dec(l, g[l]);
+      walls(src, x, y, a, f, dec, [](int, double v) { return v; });
+      mo = site_moments([&](int l) { return f[l]; });
     }
-    walls(src, x, y, a, f, dec, [](int, double v) { return v; });
-    sf = site_fields(site_moments([&](int l) { return f[l]; }), a);
+    sf = site_fields(mo, a);
   }
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) s_lam[l][tid] = __ldg(lam_in + sidx(a, l, y, x));

@@ -46,8 +46,11 @@ struct Codec<LBM_FP32_SHIFTED> {
 // it at 96 registers (5 blocks per SM, some spills) measured 27% faster than
 // the unconstrained 163 registers (3 blocks).  The double-float collide gains
 // 2-3% from the same cap (60 bytes of spill, 4 -> 5 blocks per SM).
+#ifndef LBM_DF_MINB
+#define LBM_DF_MINB 5  // minimum resident blocks per SM of the double-float and regularised steps
+#endif
 template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, int F32M = FP32_ARITH_SPLIT>
-__global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? 5 : 0) step_kernel(const void* __restrict__ src_,
+__global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? LBM_DF_MINB : 0) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a, int xb, int xe) {
   using T = typename Codec<PREC>::T;
   const int x = xb + (int)blockIdx.x * BX + (int)threadIdx.x;  // columns xb <= x < xe
