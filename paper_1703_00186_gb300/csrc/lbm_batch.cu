@@ -176,10 +176,11 @@ struct ParamTable {
 };
 static_assert(sizeof(ParamTable) + sizeof(LatticeArgs) + 16 <= 32764, "kernel parameters above 32 KB");
 
-template <int TBX, int TBY, int ROWS>
-__global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
-    batch_param_kernel(const __grid_constant__ ParamTable t, const __grid_constant__ LatticeArgs m, int parity) {
-  const long long b = blockIdx.x;
+// Tile b of the group's work list (interior and seam sites; the wall rows
+// are edge sites).  COHERENT: loads through L2 only, for the persistent
+// kernel, whose blocks read what other blocks wrote in the previous step.
+template <int TBX, int TBY, int ROWS, bool COHERENT>
+__device__ __forceinline__ void param_tile(const ParamTable& t, const LatticeArgs& m, int parity, long long b) {
   int lo = 0, hi = t.n - 1;  // the last lattice whose first tile is <= b
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -221,12 +222,12 @@ __global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
       if (x >= 3 && x < lx - 3) {
         const char* s = reinterpret_cast<const char*>(src + site);
 #pragma unroll
-        for (int l = 0; l < NPOP; ++l) f[l] = __ldg(reinterpret_cast<const float*>(s + e.pull_off[l]));
+        for (int l = 0; l < NPOP; ++l) f[l] = load<COHERENT>(reinterpret_cast<const float*>(s + e.pull_off[l]));
       } else {  // the three columns next to the periodic seam on each side
         const char* s = reinterpret_cast<const char*>(src + (y + HALO) * lx);
 #pragma unroll
         for (int l = 0; l < NPOP; ++l)
-          f[l] = __ldg(reinterpret_cast<const float*>(s + e.pull_off[l]) + (wrap_x(x - vx(l), lx) + vx(l)));
+          f[l] = load<COHERENT>(reinterpret_cast<const float*>(s + e.pull_off[l]) + (wrap_x(x - vx(l), lx) + vx(l)));
       }
       collide_fp32(f, a);
       char* d = reinterpret_cast<char*>(dst + site);
@@ -236,6 +237,12 @@ __global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
   }
 }
 
+template <int TBX, int TBY, int ROWS>
+__global__ void __launch_bounds__(TBX * TBY, 5 * 128 / (TBX * TBY))
+    batch_param_kernel(const __grid_constant__ ParamTable t, const __grid_constant__ LatticeArgs m, int parity) {
+  param_tile<TBX, TBY, ROWS, false>(t, m, parity, blockIdx.x);
+}
+
 // Number of edge sites of a lattice: the three rows next to each wall.
 __host__ __device__ inline long long edge_sites(int lx, int ly) { return 6LL * lx; }
 
@@ -243,11 +250,8 @@ __host__ __device__ inline long long edge_sites(int lx, int ly) { return 6LL * l
 // leaves out): the three rows next to each wall, through the general index
 // path, the walls and the lattice's full LatticeArgs in global memory.  One thread per edge
 // site; a thread finds its lattice by binary search over the edge offsets.
-__global__ void __launch_bounds__(128) batch_edge_kernel(const __grid_constant__ ParamTable t,
-                                                         const __grid_constant__ LatticeArgs m, int parity,
-                                                         long long total) {
-  const long long j = blockIdx.x * 128LL + threadIdx.x;
-  if (j >= total) return;
+template <bool COHERENT>
+__device__ __forceinline__ void param_edge(const ParamTable& t, int parity, long long j) {
   int lo = 0, hi = t.n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -273,10 +277,17 @@ __global__ void __launch_bounds__(128) batch_edge_kernel(const __grid_constant__
   float* __restrict__ dst = static_cast<float*>(const_cast<void*>(e.f[parity ^ 1]));
   Codec32 codec{&ga};
   float f[NPOP];
-  pull(src, x, y, ga, f);
-  walls(src, x, y, ga, f, codec, [&](int l, double v) { return codec.enc(l, v); });
+  pull<float, COHERENT>(src, x, y, ga, f);
+  walls<COHERENT>(src, x, y, ga, f, codec, [&](int l, double v) { return codec.enc(l, v); });
   collide_fp32(f, ga);
   store_site(dst, x, y, ga, f);
+}
+
+__global__ void __launch_bounds__(128) batch_edge_kernel(const __grid_constant__ ParamTable t,
+                                                         const __grid_constant__ LatticeArgs m, int parity,
+                                                         long long total) {
+  const long long j = blockIdx.x * 128LL + threadIdx.x;
+  if (j < total) param_edge<false>(t, parity, j);
 }
 
 // Grid barrier of the persistent kernel with a bounded wait.  State in global
@@ -349,6 +360,24 @@ __global__ void __launch_bounds__(128, PREC == LBM_FP32_SHIFTED ? 5 : 0) batch_p
     const int parity = (parity0 + st) & 1;
     for (long long b = blockIdx.x; b < tiles; b += gridDim.x)
       batch_tile<PREC, 32, 4, DFARITH, true, 8>(ent, tile_start, tile_lattice, parity, b, sa, s_src, s_dst);
+    if (st + 1 < steps && !grid_barrier(bar, gridDim.x, budget_ns)) return;
+  }
+}
+
+// The persistent form of the parameter-table kernel (FP32-store batches of
+// at most kParamLattices lattices): each step, blocks stride over the tile
+// list and then over the edge sites, and meet at the bounded grid barrier;
+// loads go through L2 (other blocks wrote the state in the previous step).
+__global__ void __launch_bounds__(128, 4) batch_param_persistent_kernel(const __grid_constant__ ParamTable t,
+                                                                        const __grid_constant__ LatticeArgs m,
+                                                                        long long tiles, long long edges,
+                                                                        int parity0, int steps, GridBarrier* bar,
+                                                                        unsigned long long budget_ns) {
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int st = 0; st < steps; ++st) {
+    const int parity = (parity0 + st) & 1;
+    for (long long b = blockIdx.x; b < tiles; b += gridDim.x) param_tile<32, 4, 8, true>(t, m, parity, b);
+    for (long long j = blockIdx.x * 128LL + tid; j < edges; j += gridDim.x * 128LL) param_edge<true>(t, parity, j);
     if (st + 1 < steps && !grid_barrier(bar, gridDim.x, budget_ns)) return;
   }
 }
@@ -875,6 +904,31 @@ int launch_persistent(lbm_batch* b, int n, unsigned long long budget_ns) {
   return bcuda(b, cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(32, 4), args, 0, b->stream),
                "persistent step");
 }
+// The parameter-table persistent kernel: one group, the 32 x 4 x 8 tiling.
+int launch_param_persistent(lbm_batch* b, int n, unsigned long long budget_ns) {
+  static_assert(kParamRows[kParamTiles - 1] == 8, "the persistent kernel uses the 8-row tiling");
+  auto kernel = batch_param_persistent_kernel;
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  int rc = bcuda(b, cudaGetDevice(&dev), "persistent step");
+  if (!rc) rc = bcuda(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "persistent step");
+  if (!rc) rc = bcuda(b, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "persistent step");
+  if (!rc) rc = bcuda(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0), "persistent step");
+  if (rc) return rc;
+  if (!coop || per_sm < 1) return bfail(b, LBM_ERR_INVALID, "persistent step: cooperative launch unavailable");
+  const ParamTable& t = b->ptab[kParamTiles - 1][0];
+  long long tiles = b->pblocks[kParamTiles - 1][0], edges = b->pedges[kParamTiles - 1][0];
+  const unsigned int grid = (unsigned int)std::max<long long>(
+      1, std::min<long long>((long long)per_sm * sms, std::max(tiles, (edges + 127) / 128)));
+  rc = bcuda(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream), "persistent step");
+  if (rc) return rc;
+  const LatticeArgs& m = b->args[0];
+  int parity = b->parity, steps = n;
+  GridBarrier* bar = b->d_bar;
+  void* args[] = {(void*)&t, (void*)&m, (void*)&tiles, (void*)&edges, (void*)&parity, (void*)&steps, (void*)&bar,
+                  (void*)&budget_ns};
+  return bcuda(b, cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(32, 4), args, 0, b->stream),
+               "persistent step");
+}
 }  // namespace
 
 extern "C" {
@@ -885,7 +939,9 @@ int lbm_batch_step_persistent(lbm_batch* b, int n) {
   if (n == 0) return LBM_OK;
   const unsigned long long budget = 2000000000ull;  // 2 s per barrier wait
   int rc;
-  if (b->precision == LBM_FP64_DF)
+  if (b->param_ok && b->ptab[kParamTiles - 1].size() == 1)
+    rc = launch_param_persistent(b, n, budget);
+  else if (b->precision == LBM_FP64_DF)
     rc = launch_persistent<LBM_FP64, true>(b, n, budget);
   else if (b->precision == LBM_FP64)
     rc = launch_persistent<LBM_FP64, false>(b, n, budget);

@@ -223,3 +223,24 @@ def test_parameter_table_groups_match_per_lattice_launches(tile):
         sa = a.state(i).cpu().numpy().astype(np.float64) + w
         sb = b.state(i).cpu().numpy().astype(np.float64) + w
         assert plane_err(sb, sa) <= 1e-6, i
+
+
+def test_parameter_table_persistent_launch_matches_the_graph():
+    # FP32 batch of at most 64 lattices: lbm_batch_step_persistent runs the
+    # parameter-table kernel as one cooperative launch (L2-coherent loads,
+    # bounded grid barrier); against the graph of the same kernel's tiles
+    specs, flds = build("fp32")
+    a = Batch(specs, precision="fp32")
+    b = Batch(specs, precision="fp32")
+    a.set_tile(12)
+    for i, f in enumerate(flds):
+        a.init(i, *f)
+        b.init(i, *f)
+    a.step(4)
+    b.step_persistent(4)
+    assert a.status() == 0 and b.status() == 0
+    for i in range(len(specs)):
+        w = K["w"][:, None, None] * specs[i]["rho0"]
+        sa = a.state(i).cpu().numpy().astype(np.float64) + w
+        sb = b.state(i).cpu().numpy().astype(np.float64) + w
+        assert plane_err(sb, sa) <= 1e-6, i
