@@ -105,12 +105,16 @@ int lbm_batch_step(lbm_batch* b, int n);
 
 /* Advance every lattice by n >= 0 steps with ONE persistent cooperative
  * launch: blocks stride over the tile list (32 x 4 blocks, 8 rows per
- * thread) and meet at a grid
- * barrier between steps.  Every barrier wait is bounded (2 s of global time or
+ * thread) and meet at a grid barrier between steps.  LBM_FP32_SHIFTED
+ * batches of at most 64 lattices whose lattices each hold fewer than 2^31
+ * elements run the parameter-table kernel (every lattice's constants in the
+ * kernel parameters; after the tiles, the blocks stride over the wall-row
+ * sites); other batches stage each tile's constants in shared memory.  Every barrier wait is bounded (2 s of global time or
  * 2^24 polls); if a wait gives up, the kernel sets a status flag and all
  * blocks return, and lbm_batch_status() reports LBM_ERR_TIMEOUT.  Same
- * results as lbm_batch_step (the loads use the L2-coherent path because each
- * step reads what other blocks wrote in the step before). */
+ * results as lbm_batch_step up to rounding (the loads use the L2-coherent
+ * path because each step reads what other blocks wrote in the step
+ * before). */
 int lbm_batch_step_persistent(lbm_batch* b, int n);
 
 /* Self-test of the bounded wait: launches a two-block kernel whose grid
