@@ -175,6 +175,15 @@ int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux,
  * other; the buffers then swap roles. */
 int lbm_step(lbm_ctx* ctx, int n);
 
+/* The same n >= 0 steps as lbm_step, replayed as one CUDA graph launch on
+ * the context's stream: the n step launches are captured once per (n,
+ * current buffer) on a private stream, instantiated and cached in the
+ * context (released by lbm_destroy).  For small lattices, whose steps are
+ * shorter than their launch overhead.  Bit-identical results to lbm_step.
+ * The first call for a given n captures; make it outside any stream capture
+ * of the caller's own. */
+int lbm_step_graph(lbm_ctx* ctx, int n);
+
 /* One time step from state src into state dst (caller buffers in the
  * context's precision, must not alias), leaving the context's own buffers and
  * current state untouched.  Used to recompute checkpointed trajectories. */

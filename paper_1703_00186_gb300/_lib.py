@@ -65,6 +65,7 @@ SIGNATURES = {
     "lbm_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_step": (c_int, [c_void_p, c_int]),
     "lbm_step_from": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "lbm_step_graph": (c_int, [c_void_p, c_int]),
     "lbm_current": (c_void_p, [c_void_p]),
     "lbm_swap": (c_int, [c_void_p]),
     "lbm_step_columns": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int]),

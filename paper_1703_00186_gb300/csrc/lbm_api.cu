@@ -6,8 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <utility>
 
 #include "lbm_internal.h"
 
@@ -219,6 +221,8 @@ struct lbm_ctx {
   size_t bytes;
   cudaStream_t stream;
   unsigned int* dev;  // [0] status word, [1] finite flag
+  cudaStream_t capture = nullptr;                           // private stream for graph capture
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (n, start buffer) -> n steps
   char err[512];
 };
 
@@ -298,6 +302,8 @@ void lbm_destroy(lbm_ctx* c) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->dev);
   }
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  if (c->capture) cudaStreamDestroy(c->capture);
   delete c;
 }
 
@@ -324,6 +330,43 @@ int lbm_step(lbm_ctx* c, int n) {
     if (e != cudaSuccess) return cuda_check(c, e, "lbm_step");
     c->cur ^= 1;
   }
+  return LBM_OK;
+}
+
+int lbm_step_graph(lbm_ctx* c, int n) {
+  if (!c) return LBM_ERR_INVALID;
+  if (n < 0) return fail(c, LBM_ERR_INVALID, "lbm_step_graph: n < 0");
+  if (n == 0) return LBM_OK;
+  const auto key = std::make_pair(n, c->cur);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    if (!c->capture && cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+      c->capture = nullptr;
+      return cuda_check(c, cudaGetLastError(), "lbm_step_graph: stream");
+    }
+    int rc = cuda_check(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal), "lbm_step_graph");
+    if (rc) return rc;
+    cudaError_t le = cudaSuccess;
+    int cur = c->cur;
+    for (int i = 0; i < n && le == cudaSuccess; ++i) {
+      le = launch_step(c->p.precision, true, c->buf[cur], c->buf[1 - cur], c->args, c->capture);
+      cur ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->capture, &g);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_check(c, le != cudaSuccess ? le : ee, "lbm_step_graph: capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    rc = cuda_check(c, cudaGraphInstantiate(&exec, g, 0), "lbm_step_graph: instantiate");
+    cudaGraphDestroy(g);
+    if (rc) return rc;
+    it = c->graphs.emplace(key, exec).first;
+  }
+  const int rc = cuda_check(c, cudaGraphLaunch(it->second, c->stream), "lbm_step_graph: launch");
+  if (rc) return rc;
+  c->cur ^= (n & 1);
   return LBM_OK;
 }
 

@@ -147,8 +147,12 @@ class Lattice:
         self._keep = f  # alive until the next call on this stream
         return self
 
-    def step(self, n: int = 1):
-        self._check(self.lib.lbm_step(self.ctx, int(n)))
+    def step(self, n: int = 1, graph: bool = False):
+        """n time steps; graph=True replays them as one cached CUDA graph
+        launch (same results; for small lattices, whose steps are shorter
+        than a kernel launch)."""
+        fn = self.lib.lbm_step_graph if graph else self.lib.lbm_step
+        self._check(fn(self.ctx, int(n)))
         return self
 
     def step_from(self, src: torch.Tensor, dst: torch.Tensor):
