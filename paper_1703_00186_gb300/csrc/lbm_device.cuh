@@ -957,6 +957,173 @@ __device__ __forceinline__ void collide_fp64_reg_staged(const double (&f)[NPOP],
   }
 }
 
+// The regularised collide with its integer-weighted sums grouped.  The 18
+// +- pairs fall into x-axis pairs (a, 0), y-axis pairs (0, b) and six groups
+// {(a, b), (-a, b)}.  A monomial xi_x^c xi_y^e takes the same value on both
+// members of a +- pair up to the sign (-1)^(c+e), and on the two pairs of a
+// group up to the sign (-1)^c, so every moment N_ce is a short integer
+// combination of the pair sums s and differences d and of the group sums and
+// differences of those; in the reconstruction, likewise, the even and odd
+// parts of R(xi) for the four populations of a group come from four partial
+// sums.  Compile-time weights replace the table-driven loops of
+// collide_fp64_reg_staged, and about half of the fixed-point operations go.
+// The sums are exact either way, so the results are bit-identical.
+struct RegAcc {
+  Fix96 S[4], T[4], U[4], V[4], Y, N22, N11, N31, N13, N21, N12;
+};
+
+// k x for a small positive integer k (a constant after inlining).
+__device__ __forceinline__ Fix96 fix_scale(Fix96 x, int k) {
+  return k == 1 ? x : fix_mad(Fix96{0u, 0u, 0u}, x, (unsigned)k);
+}
+
+// acc + k x, or k x alone where acc has not been set yet (FIRST).
+template <bool FIRST>
+__device__ __forceinline__ Fix96 fix_acc(Fix96 acc, Fix96 x, int k) {
+  return FIRST ? fix_scale(x, k) : fix_axpy(acc, x, k);
+}
+
+// Group {(A, B), (-A, B)}: pairs kp (A, B) and km (-A, B).  The axis pairs
+// (A, 0) and (0, B) come first, so S, T, U, V are already set; FIRST marks
+// the group (1, 1) that opens the six mixed moments.
+template <int A, int B, bool FIRST, typename F>
+__device__ __forceinline__ void reg_acc_diag(RegAcc& m, const F& f, int kp, int km, bool& ok) {
+  const Fix96 pp = to_fix(f(2 * kp + 1), ok), pm = to_fix(f(2 * kp + 2), ok);
+  const Fix96 mp = to_fix(f(2 * km + 1), ok), mm = to_fix(f(2 * km + 2), ok);
+  const Fix96 sp = fix_add(pp, pm), sm = fix_add(mp, mm), dp = fix_sub(pp, pm), dm = fix_sub(mp, mm);
+  const Fix96 Gs = fix_add(sp, sm), Hs = fix_sub(sp, sm), Gd = fix_add(dp, dm), Hd = fix_sub(dp, dm);
+  m.S[A] = fix_add(m.S[A], Gs);
+  m.T[B] = fix_add(m.T[B], Gs);
+  m.N22 = fix_acc<FIRST>(m.N22, Gs, A * A * B * B);
+  m.N11 = fix_acc<FIRST>(m.N11, Hs, A * B);
+  m.N31 = fix_acc<FIRST>(m.N31, Hs, A * A * A * B);
+  m.N13 = fix_acc<FIRST>(m.N13, Hs, A * B * B * B);
+  m.V[B] = fix_add(m.V[B], Gd);
+  m.N21 = fix_acc<FIRST>(m.N21, Gd, A * A * B);
+  m.U[A] = fix_add(m.U[A], Hd);
+  m.N12 = fix_acc<FIRST>(m.N12, Hd, A * B * B);
+}
+
+// Pair (A, 0): opens S[A] and U[A].
+template <int A, typename F>
+__device__ __forceinline__ void reg_acc_axis_x(RegAcc& m, const F& f, int k, bool& ok) {
+  const Fix96 p = to_fix(f(2 * k + 1), ok), q = to_fix(f(2 * k + 2), ok);
+  m.S[A] = fix_add(p, q);
+  m.U[A] = fix_sub(p, q);
+}
+
+// Pair (0, B): opens T[B] and V[B] (and Y with B = 1).
+template <int B, typename F>
+__device__ __forceinline__ void reg_acc_axis_y(RegAcc& m, const F& f, int k, bool& ok) {
+  const Fix96 p = to_fix(f(2 * k + 1), ok), q = to_fix(f(2 * k + 2), ok);
+  const Fix96 s = fix_add(p, q);
+  m.T[B] = s;
+  m.Y = B == 1 ? s : fix_add(m.Y, s);
+  m.V[B] = fix_sub(p, q);
+}
+
+// Populations of pair k from the even part ev and odd part od of R(xi).
+__device__ __forceinline__ void reg_store_pair(double* __restrict__ dst, const LatticeArgs& a, int k, Fix96 ev,
+                                               Fix96 od, int x, int y) {
+  const double w = a.w_shell[pair_shell(k)];
+  dst[sidx(a, 2 * k + 1, y, x)] = w * fix_to_double(fix_add(ev, od));
+  dst[sidx(a, 2 * k + 2, y, x)] = w * fix_to_double(fix_sub(ev, od));
+}
+
+// The populations are staged in shared memory (s_f[l][tid]) so that the
+// accumulators, not 37 float64 values, hold the registers; sites with a
+// population or a coefficient outside the fixed-point range take
+// collide_fp64_reg.
+template <int NT>
+__device__ __forceinline__ void collide_fp64_reg_grouped(const double (&f_in)[NPOP], const LatticeArgs& a,
+                                                         double (*s_f)[NT], int tid, double* __restrict__ dst,
+                                                         int x, int y) {
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) s_f[l][tid] = f_in[l];
+  const auto f = [&](int l) { return s_f[l][tid]; };
+  bool ok = true;
+  double N[15];
+  {
+    RegAcc m;
+    reg_acc_axis_x<1>(m, f, 0, ok);
+    reg_acc_axis_y<1>(m, f, 1, ok);
+    reg_acc_diag<1, 1, true>(m, f, 2, 3, ok);
+    reg_acc_axis_x<2>(m, f, 4, ok);
+    reg_acc_axis_y<2>(m, f, 5, ok);
+    reg_acc_diag<2, 1, false>(m, f, 6, 9, ok);
+    reg_acc_diag<1, 2, false>(m, f, 7, 8, ok);
+    reg_acc_diag<2, 2, false>(m, f, 10, 11, ok);
+    reg_acc_axis_x<3>(m, f, 12, ok);
+    reg_acc_axis_y<3>(m, f, 13, ok);
+    reg_acc_diag<3, 1, false>(m, f, 14, 17, ok);
+    reg_acc_diag<1, 3, false>(m, f, 15, 16, ok);
+    const Fix96 f0 = to_fix(f(0), ok);
+    N[0] = fix_to_double(fix_add(fix_add(f0, fix_add(m.S[1], m.S[2])), fix_add(m.S[3], m.Y)));
+    N[1] = fix_to_double(fix_mad(fix_mad(m.S[1], m.S[2], 4u), m.S[3], 9u));
+    N[2] = fix_to_double(fix_mad(fix_mad(m.T[1], m.T[2], 4u), m.T[3], 9u));
+    N[3] = fix_to_double(fix_mad(fix_mad(m.S[1], m.S[2], 16u), m.S[3], 81u));
+    N[4] = fix_to_double(m.N22);
+    N[5] = fix_to_double(fix_mad(fix_mad(m.T[1], m.T[2], 16u), m.T[3], 81u));
+    N[6] = fix_to_double(fix_mad(fix_mad(m.U[1], m.U[2], 2u), m.U[3], 3u));
+    N[7] = fix_to_double(fix_mad(fix_mad(m.U[1], m.U[2], 8u), m.U[3], 27u));
+    N[8] = fix_to_double(m.N12);
+    N[9] = fix_to_double(fix_mad(fix_mad(m.V[1], m.V[2], 2u), m.V[3], 3u));
+    N[10] = fix_to_double(fix_mad(fix_mad(m.V[1], m.V[2], 8u), m.V[3], 27u));
+    N[11] = fix_to_double(m.N21);
+    N[12] = fix_to_double(m.N11);
+    N[13] = fix_to_double(m.N31);
+    N[14] = fix_to_double(m.N13);
+  }
+  double Rv[15];
+  if (ok) reg_coefficients(N, a, Rv);
+  Fix96 X[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) X[i] = to_fix(ok ? Rv[i] : 0.0, ok);
+  if (!ok) {  // float64 path for this site
+    double g[NPOP];
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) g[l] = f(l);
+    collide_fp64_reg(g, a);
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
+    return;
+  }
+  // X order: 00 20 02 40 22 04 10 30 12 01 03 21 11 31 13
+  dst[sidx(a, 0, y, x)] = a.w_shell[0] * Rv[0];
+  auto axis_x = [&](int k, int c) {  // pair (c, 0)
+    const Fix96 ev = fix_axpy(fix_axpy(X[0], X[1], c * c), X[3], c * c * c * c);
+    const Fix96 od = fix_axpy(fix_scale(X[6], c), X[7], c * c * c);
+    reg_store_pair(dst, a, k, ev, od, x, y);
+  };
+  auto axis_y = [&](int k, int c) {  // pair (0, c)
+    const Fix96 ev = fix_axpy(fix_axpy(X[0], X[2], c * c), X[5], c * c * c * c);
+    const Fix96 od = fix_axpy(fix_scale(X[9], c), X[10], c * c * c);
+    reg_store_pair(dst, a, k, ev, od, x, y);
+  };
+  auto diag = [&](int kp, int km, int A, int B) {  // pairs (A, B) and (-A, B)
+    const Fix96 Ae = fix_axpy(fix_axpy(fix_axpy(fix_axpy(fix_axpy(X[0], X[1], A * A), X[2], B * B), X[3], A * A * A * A),
+                                       X[4], A * A * B * B),
+                              X[5], B * B * B * B);
+    const Fix96 Bo = fix_axpy(fix_axpy(fix_scale(X[12], A * B), X[13], A * A * A * B), X[14], A * B * B * B);
+    const Fix96 Co = fix_axpy(fix_axpy(fix_scale(X[6], A), X[7], A * A * A), X[8], A * B * B);
+    const Fix96 Do = fix_axpy(fix_axpy(fix_scale(X[9], B), X[10], B * B * B), X[11], A * A * B);
+    reg_store_pair(dst, a, kp, fix_add(Ae, Bo), fix_add(Co, Do), x, y);
+    reg_store_pair(dst, a, km, fix_sub(Ae, Bo), fix_sub(Do, Co), x, y);
+  };
+  axis_x(0, 1);
+  axis_y(1, 1);
+  diag(2, 3, 1, 1);
+  axis_x(4, 2);
+  axis_y(5, 2);
+  diag(6, 9, 2, 1);
+  diag(7, 8, 1, 2);
+  diag(10, 11, 2, 2);
+  axis_x(12, 3);
+  axis_y(13, 3);
+  diag(14, 17, 3, 1);
+  diag(15, 16, 1, 3);
+}
+
 // Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.
 __device__ __forceinline__ void equilibrium(double rho, double ux, double uy, double T,
                                             const LatticeArgs& a, double (&f)[NPOP]) {

@@ -47,10 +47,13 @@ struct Codec<LBM_FP32_SHIFTED> {
 // the unconstrained 163 registers (3 blocks).  The double-float collide gains
 // 2-3% from the same cap (60 bytes of spill, 4 -> 5 blocks per SM).
 #ifndef LBM_DF_MINB
-#define LBM_DF_MINB 5  // minimum resident blocks per SM of the double-float and regularised steps
+#define LBM_DF_MINB 5  // minimum resident blocks per SM of the double-float step
+#endif
+#ifndef LBM_REG_MINB
+#define LBM_REG_MINB 4  // minimum resident blocks per SM of the regularised step
 #endif
 template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, int F32M = FP32_ARITH_SPLIT>
-__global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? LBM_DF_MINB : 0) step_kernel(const void* __restrict__ src_,
+__global__ void __launch_bounds__(BX * BY, REG ? LBM_REG_MINB : DFARITH ? LBM_DF_MINB : 0) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a, int xb, int xe) {
   using T = typename Codec<PREC>::T;
   const int x = xb + (int)blockIdx.x * BX + (int)threadIdx.x;  // columns xb <= x < xe
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(BX * BY, (REG || DFARITH) ? LBM_DF_MINB : 0) s
   if constexpr (PREC == LBM_FP64 && REG) {
     if (COLLIDE) {
       __shared__ double s_f[NPOP][BX * BY];
-      collide_fp64_reg_staged<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
+      collide_fp64_reg_grouped<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
       return;
     }
   }

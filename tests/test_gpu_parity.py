@@ -311,6 +311,26 @@ def test_one_step_parity_regularized(lx, ly, periodic_y):
     assert plane_err(lat.state().cpu().numpy(), want) <= 1e-12
 
 
+def test_one_step_parity_regularized_outside_the_fixed_point_range():
+    # Sites whose pulled populations include one >= 4 (or whose projection
+    # coefficients leave the fixed-point range) relax in float64; tiny, zero
+    # and negative populations stay on the fixed-point path.  Both must match.
+    lx, ly = 37, 11
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.9, t_bottom=1.1)
+    f = noisy_state(lx, ly, 431, eps=0.05)
+    phys = f[:, 3:-3]
+    phys[9, 5, 20] = 4.5
+    phys[0, 2, 7] = 6.0
+    phys[21, 8, 30] = -0.01
+    phys[11, 1, 3] = 0.0
+    phys[30, 6, 33] = 1e-300
+    want = M.step_regularized(f, p)
+    lat = Lattice(lx, ly, tau=p.tau, g=p.g, t_top=p.t_top, t_bottom=p.t_bottom, regularized=True)
+    lat.set_state(to_dev(f))
+    lat.step(1)
+    assert plane_err(lat.state().cpu().numpy(), want) <= 1e-12
+
+
 def test_rayleigh_taylor_64x128_100_steps_regularized():
     rho, ux, uy, T, tt, tb = synth.rt_fields(64, 128, 4, 0)
     p = M.Params(64, 128, tau=0.8, g=1e-4, t_top=tt, t_bottom=tb)
