@@ -98,6 +98,40 @@ __device__ __forceinline__ Fix96 to_fix(double v, bool& ok) {
   return r;
 }
 
+// to_fix for |v| < 2^(EMAX - 1022), EMAX <= kFixE0 + 42 (|v| < 2^12): the
+// significand may also move past the first word (left shifts of 32 to 42).
+// `ok` is cleared above that bound, for infinities and for NaNs.  Used for
+// the coefficients of a polynomial whose evaluated sums the caller keeps
+// inside the format's range by choosing EMAX per coefficient.
+template <int EMAX>
+__device__ __forceinline__ Fix96 to_fix_upto(double v, bool& ok) {
+  static_assert(EMAX <= kFixE0 + 42, "the significand must stay below the sign bit");
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  ok = ok && e <= EMAX;
+  const unsigned m1 = (hi & 0xfffffu) | (e != 0 ? 0x100000u : 0u);
+  const int s = e - kFixE0;
+  Fix96 r;
+  if (s >= 32) {
+    const int t = min(s - 32, 10);
+    r.w0 = 0u;
+    r.w1 = lo << t;
+    r.w2 = __funnelshift_l(lo, m1, t);
+  } else if (s >= 0) {
+    const int t = s;
+    r.w0 = lo << t;
+    r.w1 = __funnelshift_l(lo, m1, t);
+    r.w2 = __funnelshift_l(m1, 0u, t);
+  } else {
+    const int t = -s;
+    r.w0 = t < 32 ? __funnelshift_r(lo, m1, t) : (t < 53 ? m1 >> (t - 32) : 0u);
+    r.w1 = t < 32 ? m1 >> t : 0u;
+    r.w2 = 0u;
+  }
+  if (hi >> 31) r = fix_sub(Fix96{0u, 0u, 0u}, r);
+  return r;
+}
+
 // Exact conversion of a float32 with |v| < 4 (biased exponent <= 128):
 // v = M 2^(e - 150) for the 24-bit significand M, i.e. M shifted left by
 // e - 68 <= 60 places on the 2^-82 grid.  Values below 2^-58 keep their bits

@@ -115,6 +115,9 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
     if constexpr (PREC == LBM_FP64 && DFARITH) {
       __shared__ double s_f[NPOP][TBX * TBY];
       collide_fp64_df<TBX * TBY>(f, a, s_f, tid, dst, x, y);
+    } else if constexpr (PREC == LBM_FP64 && TBX * TBY <= 128) {
+      __shared__ double s_f[NPOP][TBX * TBY];  // within the 48 KB of static shared memory
+      collide_fp64_fix<TBX * TBY>(f, a, s_f, tid, dst, x, y);
     } else {
       if constexpr (PREC == LBM_FP64)
         collide_fp64(f, a);

@@ -857,104 +857,13 @@ __device__ __forceinline__ void reg_reconstruct_f64(const double (&Rv)[15], cons
 // xi_x^c xi_y^d and G the (block-diagonal) Gram matrix of the monomials; the
 // new populations are w_l R(xi_l) with R = omega rho P + (1 - omega) q, P the
 // equilibrium polynomial expanded in the same monomials.
-// This is the float64 evaluation; collide_fp64_reg_staged below forms the
+// This is the float64 evaluation; collide_fp64_reg_grouped below forms the
 // integer-weighted sums in fixed point.
 __device__ __forceinline__ void collide_fp64_reg(double (&f)[NPOP], const LatticeArgs& a) {
   double N[15], Rv[15];
   reg_moments_f64(f, N);
   reg_coefficients(N, a, Rv);
   reg_reconstruct_f64(Rv, a, f);
-}
-
-// xi_k^(c_i, e_i) for pair representative k and monomial i (order of N).
-static __constant__ signed char c_reg_coef[NPAIR][15] = {
-    {1, 1, 0, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0},
-    {1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 1, 0, 0, 0, 0},
-    {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
-    {1, 1, 1, 1, 1, 1, -1, -1, -1, 1, 1, 1, -1, -1, -1},
-    {1, 4, 0, 16, 0, 0, 2, 8, 0, 0, 0, 0, 0, 0, 0},
-    {1, 0, 4, 0, 0, 16, 0, 0, 0, 2, 8, 0, 0, 0, 0},
-    {1, 4, 1, 16, 4, 1, 2, 8, 2, 1, 1, 4, 2, 8, 2},
-    {1, 1, 4, 1, 4, 16, 1, 1, 4, 2, 8, 2, 2, 2, 8},
-    {1, 1, 4, 1, 4, 16, -1, -1, -4, 2, 8, 2, -2, -2, -8},
-    {1, 4, 1, 16, 4, 1, -2, -8, -2, 1, 1, 4, -2, -8, -2},
-    {1, 4, 4, 16, 16, 16, 2, 8, 8, 2, 8, 8, 4, 16, 16},
-    {1, 4, 4, 16, 16, 16, -2, -8, -8, 2, 8, 8, -4, -16, -16},
-    {1, 9, 0, 81, 0, 0, 3, 27, 0, 0, 0, 0, 0, 0, 0},
-    {1, 0, 9, 0, 0, 81, 0, 0, 0, 3, 27, 0, 0, 0, 0},
-    {1, 9, 1, 81, 9, 1, 3, 27, 3, 1, 1, 9, 3, 27, 3},
-    {1, 1, 9, 1, 9, 81, 1, 1, 9, 3, 27, 3, 3, 3, 27},
-    {1, 1, 9, 1, 9, 81, -1, -1, -9, 3, 27, 3, -3, -3, -27},
-    {1, 9, 1, 81, 9, 1, -3, -27, -3, 1, 1, 9, -3, -27, -3}};
-
-__host__ __device__ constexpr bool reg_odd(int i) { return i >= 6 && i < 12; }
-
-// acc + c x for a small integer c read at run time (the same for the whole
-// warp, so the branches do not diverge).
-__device__ __forceinline__ Fix96 fix_axpy_rt(Fix96 acc, Fix96 x, int c) {
-  if (c == 0) return acc;
-  const unsigned m = (unsigned)(c < 0 ? -c : c);
-  const Fix96 t = m == 1u ? x : fix_mad(Fix96{0u, 0u, 0u}, x, m);
-  return c < 0 ? fix_sub(acc, t) : fix_add(acc, t);
-}
-
-// Regularised collide with its integer-weighted sums on the integer pipe:
-// the 15 monomial moments N and the even / odd parts of R(xi) for every pair
-// are exact 96-bit fixed-point sums (rounded once each), in loops rolled over
-// the pairs (populations staged in shared memory) so that fifteen
-// accumulators fit the register file; the coefficients R stay float64 and the
-// new populations w_l R(xi_l) go straight to dst.  Sites with a population
-// or a coefficient outside the fixed-point range take collide_fp64_reg.
-template <int NT>
-__device__ __forceinline__ void collide_fp64_reg_staged(const double (&f)[NPOP], const LatticeArgs& a,
-                                                        double (*s_f)[NT], int tid, double* __restrict__ dst,
-                                                        int x, int y) {
-#pragma unroll
-  for (int l = 0; l < NPOP; ++l) s_f[l][tid] = f[l];
-  bool ok = true;
-  double N[15];
-  {
-    Fix96 acc[15];
-    acc[0] = to_fix(s_f[0][tid], ok);
-#pragma unroll
-    for (int i = 1; i < 15; ++i) acc[i] = Fix96{0u, 0u, 0u};
-#pragma unroll 1
-    for (int k = 0; k < NPAIR; ++k) {
-      const Fix96 p = to_fix(s_f[2 * k + 1][tid], ok), m = to_fix(s_f[2 * k + 2][tid], ok);
-      const Fix96 sk = fix_add(p, m), dk = fix_sub(p, m);
-#pragma unroll
-      for (int i = 0; i < 15; ++i) acc[i] = fix_axpy_rt(acc[i], reg_odd(i) ? dk : sk, c_reg_coef[k][i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 15; ++i) N[i] = fix_to_double(acc[i]);
-  }
-  double Rv[15];
-  if (ok) reg_coefficients(N, a, Rv);
-  Fix96 X[15];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) X[i] = to_fix(ok ? Rv[i] : 0.0, ok);
-  if (!ok) {  // float64 path for this site
-    double g[NPOP];
-#pragma unroll
-    for (int l = 0; l < NPOP; ++l) g[l] = s_f[l][tid];
-    collide_fp64_reg(g, a);
-#pragma unroll
-    for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
-    return;
-  }
-  dst[sidx(a, 0, y, x)] = a.w_shell[0] * Rv[0];
-#pragma unroll 1
-  for (int k = 0; k < NPAIR; ++k) {
-    Fix96 ev = X[0], od{0u, 0u, 0u};
-#pragma unroll
-    for (int i = 1; i < 15; ++i) {
-      if (reg_odd(i)) od = fix_axpy_rt(od, X[i], c_reg_coef[k][i]);
-      else ev = fix_axpy_rt(ev, X[i], c_reg_coef[k][i]);
-    }
-    const double w = a.w_shell[pair_shell(k)];
-    dst[sidx(a, 2 * k + 1, y, x)] = w * fix_to_double(fix_add(ev, od));
-    dst[sidx(a, 2 * k + 2, y, x)] = w * fix_to_double(fix_sub(ev, od));
-  }
 }
 
 // The regularised collide with its integer-weighted sums grouped.  The 18
@@ -965,9 +874,9 @@ __device__ __forceinline__ void collide_fp64_reg_staged(const double (&f)[NPOP],
 // combination of the pair sums s and differences d and of the group sums and
 // differences of those; in the reconstruction, likewise, the even and odd
 // parts of R(xi) for the four populations of a group come from four partial
-// sums.  Compile-time weights replace the table-driven loops of
-// collide_fp64_reg_staged, and about half of the fixed-point operations go.
-// The sums are exact either way, so the results are bit-identical.
+// sums.  Every sum is exact in fixed point (rounded once to float64), so the
+// grouping changes the operation count (about half that of summing monomial
+// by monomial), not the result.
 struct RegAcc {
   Fix96 S[4], T[4], U[4], V[4], Y, N22, N11, N31, N13, N21, N12;
 };
@@ -1020,6 +929,70 @@ __device__ __forceinline__ void reg_acc_axis_y(RegAcc& m, const F& f, int k, boo
   m.T[B] = s;
   m.Y = B == 1 ? s : fix_add(m.Y, s);
   m.V[B] = fix_sub(p, q);
+}
+
+// Fixed-point coefficients X of a polynomial in the monomials (order of N:
+// 00 20 02 40 22 04 10 30 12 01 03 21 11 31 13).  A monomial of degree n is at
+// most 3^n in magnitude at the 37 velocities, so with |X| below 2^10, 2^8,
+// 2^6, 2^4 and 2^2 for degrees 0 to 4 every value of the polynomial, and so
+// every sum poly_eval_grouped rounds, stays below 2^13 (7636 at most), inside
+// the format; `ok` is cleared otherwise.
+__device__ __forceinline__ void poly_to_fix(const double (&c)[15], Fix96 (&X)[15], bool& ok) {
+  constexpr int E0 = kFixE0 + 39, E1 = kFixE0 + 37, E2 = kFixE0 + 35, E3 = kFixE0 + 33, E4 = kFixE0 + 31;
+  X[0] = to_fix_upto<E0>(c[0], ok);
+  X[1] = to_fix_upto<E2>(c[1], ok);
+  X[2] = to_fix_upto<E2>(c[2], ok);
+  X[3] = to_fix_upto<E4>(c[3], ok);
+  X[4] = to_fix_upto<E4>(c[4], ok);
+  X[5] = to_fix_upto<E4>(c[5], ok);
+  X[6] = to_fix_upto<E1>(c[6], ok);
+  X[7] = to_fix_upto<E3>(c[7], ok);
+  X[8] = to_fix_upto<E3>(c[8], ok);
+  X[9] = to_fix_upto<E1>(c[9], ok);
+  X[10] = to_fix_upto<E3>(c[10], ok);
+  X[11] = to_fix_upto<E3>(c[11], ok);
+  X[12] = to_fix_upto<E2>(c[12], ok);
+  X[13] = to_fix_upto<E4>(c[13], ok);
+  X[14] = to_fix_upto<E4>(c[14], ok);
+}
+
+// The polynomial with coefficients X at the 36 moving velocities, grouped
+// like the moments: for pair k, emit(k, ev, od) receives the even part ev and
+// the odd part od of the polynomial at +R_k (at -R_k it is ev - od).
+template <typename Emit>
+__device__ __forceinline__ void poly_eval_grouped(const Fix96 (&X)[15], Emit&& emit) {
+  auto axis_x = [&](int k, int c) {  // pair (c, 0)
+    const Fix96 ev = fix_axpy(fix_axpy(X[0], X[1], c * c), X[3], c * c * c * c);
+    const Fix96 od = fix_axpy(fix_scale(X[6], c), X[7], c * c * c);
+    emit(k, ev, od);
+  };
+  auto axis_y = [&](int k, int c) {  // pair (0, c)
+    const Fix96 ev = fix_axpy(fix_axpy(X[0], X[2], c * c), X[5], c * c * c * c);
+    const Fix96 od = fix_axpy(fix_scale(X[9], c), X[10], c * c * c);
+    emit(k, ev, od);
+  };
+  auto diag = [&](int kp, int km, int A, int B) {  // pairs (A, B) and (-A, B)
+    const Fix96 Ae = fix_axpy(fix_axpy(fix_axpy(fix_axpy(fix_axpy(X[0], X[1], A * A), X[2], B * B), X[3], A * A * A * A),
+                                       X[4], A * A * B * B),
+                              X[5], B * B * B * B);
+    const Fix96 Bo = fix_axpy(fix_axpy(fix_scale(X[12], A * B), X[13], A * A * A * B), X[14], A * B * B * B);
+    const Fix96 Co = fix_axpy(fix_axpy(fix_scale(X[6], A), X[7], A * A * A), X[8], A * B * B);
+    const Fix96 Do = fix_axpy(fix_axpy(fix_scale(X[9], B), X[10], B * B * B), X[11], A * A * B);
+    emit(kp, fix_add(Ae, Bo), fix_add(Co, Do));
+    emit(km, fix_sub(Ae, Bo), fix_sub(Do, Co));
+  };
+  axis_x(0, 1);
+  axis_y(1, 1);
+  diag(2, 3, 1, 1);
+  axis_x(4, 2);
+  axis_y(5, 2);
+  diag(6, 9, 2, 1);
+  diag(7, 8, 1, 2);
+  diag(10, 11, 2, 2);
+  axis_x(12, 3);
+  axis_y(13, 3);
+  diag(14, 17, 3, 1);
+  diag(15, 16, 1, 3);
 }
 
 // Populations of pair k from the even part ev and odd part od of R(xi).
@@ -1077,8 +1050,7 @@ __device__ __forceinline__ void collide_fp64_reg_grouped(const double (&f_in)[NP
   double Rv[15];
   if (ok) reg_coefficients(N, a, Rv);
   Fix96 X[15];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) X[i] = to_fix(ok ? Rv[i] : 0.0, ok);
+  if (ok) poly_to_fix(Rv, X, ok);
   if (!ok) {  // float64 path for this site
     double g[NPOP];
 #pragma unroll
@@ -1088,40 +1060,53 @@ __device__ __forceinline__ void collide_fp64_reg_grouped(const double (&f_in)[NP
     for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
     return;
   }
-  // X order: 00 20 02 40 22 04 10 30 12 01 03 21 11 31 13
   dst[sidx(a, 0, y, x)] = a.w_shell[0] * Rv[0];
-  auto axis_x = [&](int k, int c) {  // pair (c, 0)
-    const Fix96 ev = fix_axpy(fix_axpy(X[0], X[1], c * c), X[3], c * c * c * c);
-    const Fix96 od = fix_axpy(fix_scale(X[6], c), X[7], c * c * c);
-    reg_store_pair(dst, a, k, ev, od, x, y);
-  };
-  auto axis_y = [&](int k, int c) {  // pair (0, c)
-    const Fix96 ev = fix_axpy(fix_axpy(X[0], X[2], c * c), X[5], c * c * c * c);
-    const Fix96 od = fix_axpy(fix_scale(X[9], c), X[10], c * c * c);
-    reg_store_pair(dst, a, k, ev, od, x, y);
-  };
-  auto diag = [&](int kp, int km, int A, int B) {  // pairs (A, B) and (-A, B)
-    const Fix96 Ae = fix_axpy(fix_axpy(fix_axpy(fix_axpy(fix_axpy(X[0], X[1], A * A), X[2], B * B), X[3], A * A * A * A),
-                                       X[4], A * A * B * B),
-                              X[5], B * B * B * B);
-    const Fix96 Bo = fix_axpy(fix_axpy(fix_scale(X[12], A * B), X[13], A * A * A * B), X[14], A * B * B * B);
-    const Fix96 Co = fix_axpy(fix_axpy(fix_scale(X[6], A), X[7], A * A * A), X[8], A * B * B);
-    const Fix96 Do = fix_axpy(fix_axpy(fix_scale(X[9], B), X[10], B * B * B), X[11], A * A * B);
-    reg_store_pair(dst, a, kp, fix_add(Ae, Bo), fix_add(Co, Do), x, y);
-    reg_store_pair(dst, a, km, fix_sub(Ae, Bo), fix_sub(Do, Co), x, y);
-  };
-  axis_x(0, 1);
-  axis_y(1, 1);
-  diag(2, 3, 1, 1);
-  axis_x(4, 2);
-  axis_y(5, 2);
-  diag(6, 9, 2, 1);
-  diag(7, 8, 1, 2);
-  diag(10, 11, 2, 2);
-  axis_x(12, 3);
-  axis_y(13, 3);
-  diag(14, 17, 3, 1);
-  diag(15, 16, 1, 3);
+  poly_eval_grouped(X, [&](int k, Fix96 ev, Fix96 od) { reg_store_pair(dst, a, k, ev, od, x, y); });
+}
+
+// BGK collide (eq. 1) with the equilibrium evaluated on the integer pipe:
+//   f_l <- (1 - omega) f_l + (omega rho w_l) P(xi_l),
+// P the equilibrium polynomial of eq_monomials (the one collide_fp64
+// evaluates population by population in float64).  The moments are the exact
+// fixed-point sums of site_moments; P(xi_l) is an exact fixed-point sum of its
+// 15 coefficients with integer weights, rounded once; float64 does the site
+// fields, the coefficients, the eight shell factors omega rho w_j and one
+// multiply and one fused multiply-add per population.  The populations wait in
+// shared memory (s_f[l][tid]) for the relaxation.  Sites with a coefficient
+// outside poly_to_fix's range take collide_fp64.
+template <int NT>
+__device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], const LatticeArgs& a,
+                                                       double (*s_f)[NT], int tid, double* __restrict__ dst, int x,
+                                                       int y) {
+  const Moments mo = site_moments([&](int l) { return f[l]; });
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) s_f[l][tid] = f[l];
+  const SiteFields sf = site_fields(mo, a);
+  double P[15];
+  eq_monomials(sf, a, P);
+  bool ok = true;
+  Fix96 X[15];
+  poly_to_fix(P, X, ok);
+  if (!ok) {  // float64 path for this site
+    double g[NPOP];
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) g[l] = s_f[l][tid];
+    collide_fp64(g, a);
+#pragma unroll
+    for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
+    return sf;
+  }
+  const double wr = a.omega * sf.rho;
+  double sw[NSHELL];
+#pragma unroll
+  for (int j = 0; j < NSHELL; ++j) sw[j] = wr * a.w_shell[j];
+  dst[sidx(a, 0, y, x)] = fma(a.omc, s_f[0][tid], sw[0] * P[0]);
+  poly_eval_grouped(X, [&](int k, Fix96 ev, Fix96 od) {
+    const double w = sw[pair_shell(k)];
+    dst[sidx(a, 2 * k + 1, y, x)] = fma(a.omc, s_f[2 * k + 1][tid], w * fix_to_double(fix_add(ev, od)));
+    dst[sidx(a, 2 * k + 2, y, x)] = fma(a.omc, s_f[2 * k + 2][tid], w * fix_to_double(fix_sub(ev, od)));
+  });
+  return sf;
 }
 
 // Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.

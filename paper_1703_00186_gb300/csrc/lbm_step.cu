@@ -49,11 +49,17 @@ struct Codec<LBM_FP32_SHIFTED> {
 #ifndef LBM_DF_MINB
 #define LBM_DF_MINB 5  // minimum resident blocks per SM of the double-float step
 #endif
+#ifndef LBM_FP64_FIX
+#define LBM_FP64_FIX 1  // float64 BGK step: equilibrium polynomial on the integer pipe
+#endif
+#ifndef LBM_FP64_MINB
+#define LBM_FP64_MINB 0  // minimum resident blocks per SM of the float64 BGK step (0: no cap)
+#endif
 #ifndef LBM_REG_MINB
 #define LBM_REG_MINB 4  // minimum resident blocks per SM of the regularised step
 #endif
 template <int PREC, bool COLLIDE, bool DFARITH = false, bool REG = false, int F32M = FP32_ARITH_SPLIT>
-__global__ void __launch_bounds__(BX * BY, REG ? LBM_REG_MINB : DFARITH ? LBM_DF_MINB : 0) step_kernel(const void* __restrict__ src_,
+__global__ void __launch_bounds__(BX * BY, REG ? LBM_REG_MINB : DFARITH ? LBM_DF_MINB : (PREC == LBM_FP64 && COLLIDE) ? LBM_FP64_MINB : 0) step_kernel(const void* __restrict__ src_,
                                                        void* __restrict__ dst_, LatticeArgs a, int xb, int xe) {
   using T = typename Codec<PREC>::T;
   const int x = xb + (int)blockIdx.x * BX + (int)threadIdx.x;  // columns xb <= x < xe
@@ -95,6 +101,13 @@ __global__ void __launch_bounds__(BX * BY, REG ? LBM_REG_MINB : DFARITH ? LBM_DF
       return;
     }
   }
+  if constexpr (PREC == LBM_FP64 && LBM_FP64_FIX) {
+    if (COLLIDE) {
+      __shared__ double s_f[NPOP][BX * BY];
+      collide_fp64_fix<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
+      return;
+    }
+  }
   if (COLLIDE) {
     if constexpr (PREC == LBM_FP64) {
       collide_fp64(f, a);
@@ -130,8 +143,8 @@ __global__ void __launch_bounds__(BX * BY, 4) step_observe_kernel(const double* 
     if (fast_site(a, x)) pull_fast(src, site_off(a, y, x), a, f);
     else pull(src, x, y, a, f);
     walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
-    const SiteFields sf = collide_fp64(f, a);
-    store_site(dst, x, y, a, f);
+    __shared__ double s_f[NPOP][BX * BY];
+    const SiteFields sf = collide_fp64_fix<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
     site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy - 0.5 * a.g, sf.T, o);
   }
   constexpr unsigned kAll = 0xffffffffu;
