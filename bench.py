@@ -38,22 +38,27 @@ sys.path.insert(0, ROOT)
 METRIC = "D2Q37 MLUPS, FP64 vs FP32-store, and adjoint/forward step time ratio, 1 GB300"
 WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-5"
 
-# Algorithmic float64 work of the fused step per site, counted stage by stage
-# from the collide's formulation (an FMA counts 2 flops, the division 1/rho
-# counts 1): moment sums 110, site fields 9, gravity shift and Hermite
-# coefficients 30, per-shell terms 81, per-pair polynomial and relaxation 312
-# (18 pairs x 16 + 24 for the c.u products).  The 110 of the moment sums run
-# exactly in fixed point on the integer pipe; the other 432 on the FP64 pipe.
-# ncu counts 261 FP64 instructions per site on the current kernel (DFMA 177,
-# DMUL 72, DADD 12: 438 flops, the 432 plus the Newton steps of 1/rho).
-FP64_FLOP_PER_SITE = 542
-FP64_FLOP_PER_SITE_MOMENT_SUMS = 110
-FP64_INSTR_PER_SITE_NCU = 261
-FP64_PIPE_FLOP_PER_SITE_NCU = 2 * 177 + 72 + 12
+# Float64 work of the fused step per site, counted stage by stage from the
+# collide's formulation (an FMA counts 2 flops, the division 1/rho counts 1).
+# The plain formulation (every sum and the per-pair polynomial in float64):
+# moment sums 110, site fields 9, gravity shift and Hermite coefficients 30,
+# per-shell terms 81, per-pair polynomial and relaxation 312: 542.
+# The kernel forms the moment sums and evaluates the equilibrium polynomial at
+# the 36 moving velocities exactly in fixed point on the integer pipe; what
+# stays on the FP64 pipe is: site fields 9, gravity shift and Hermite
+# coefficients 30, the 15 monomial coefficients of the equilibrium 58, the
+# eight shell factors omega rho w_j 9, one multiply and one FMA per
+# population 111: 217.  ncu counts 160.2 FP64 instructions per site on this
+# kernel (DFMA 67.0, DMUL 85.1, DADD 8.1: 227 flops, the 217 plus the Newton
+# steps of 1/rho).
+FP64_FLOP_PER_SITE_PLAIN = 542
+FP64_FLOP_PER_SITE = 217
+FP64_INSTR_PER_SITE_NCU = 160.2
+FP64_PIPE_FLOP_PER_SITE_NCU = 227.2
 # DRAM bytes per site of the float64 step (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one 2048 x 1024 launch, 1190.35 MB / 2097152 sites;
+# dram__bytes_write.sum of one 2048 x 1024 launch, 1191.64 MB / 2097152 sites;
 # traffic grows with the site count, so a full launch is scaled by sites).
-FP64_TRAFFIC_BYTES_PER_SITE_NCU = 567.60
+FP64_TRAFFIC_BYTES_PER_SITE_NCU = 568.22
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
@@ -754,13 +759,15 @@ def main():
                                              "2048x1024 launch, scaled by sites",
                            "peak_source": ("measured FP64 FMA probe (lbm_probe_fma), this run" if fp64_peak
                                            else "nominal 1.25 TFLOP/s"),
+                           "pipe": "FP64 (the float64 work left after the exact fixed-point sums and "
+                                   "polynomial evaluation on the integer pipe)",
                            "flop_per_site": FP64_FLOP_PER_SITE,
-                           "flop_per_site_on_integer_pipe": FP64_FLOP_PER_SITE_MOMENT_SUMS,
                            "fp64_instr_per_site_ncu": FP64_INSTR_PER_SITE_NCU,
                            "fp64_issue_frac": FP64_INSTR_PER_SITE_NCU * sites / t_launch / (peak * 1e12 / 2),
-                           "fp64_pipe_only_frac": (FP64_FLOP_PER_SITE - FP64_FLOP_PER_SITE_MOMENT_SUMS) * sites
-                                                  / t_launch / 1e12 / peak,
                            "fp64_pipe_flop_per_site_ncu": FP64_PIPE_FLOP_PER_SITE_NCU,
+                           "plain_formulation_flop_per_site": FP64_FLOP_PER_SITE_PLAIN,
+                           "plain_formulation_tflops": FP64_FLOP_PER_SITE_PLAIN * sites / t_launch / 1e12,
+                           "plain_formulation_frac": FP64_FLOP_PER_SITE_PLAIN * sites / t_launch / 1e12 / peak,
                            "peak_from_units": peak_units,
                            "algorithmic_bytes_per_launch": BYTES_PER_SITE_FP64 * sites,
                            "hbm_gbs": BYTES_PER_SITE_FP64 * sites / t_launch / 1e9,

@@ -132,6 +132,39 @@ __device__ __forceinline__ Fix96 to_fix_upto(double v, bool& ok) {
   return r;
 }
 
+// Block scaling for values of no fixed magnitude (cotangents): a per-site
+// exponent D moves the whole set onto the grid, v 2^-D in fixed point and a
+// fixed-point sum s back as s 2^D.  Both are exact exponent shifts (integer
+// operations only).
+
+// Biased exponent field of a float64.
+__device__ __forceinline__ int exp_field(double v) { return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu); }
+
+// to_fix of v 2^-D for a v whose biased exponent is at most kFixEMax + D
+// (|v 2^-D| < 4), which the caller guarantees (D from the largest exponent
+// of the set).  Bits below 2^(D - 82) are dropped, subnormals give 0.
+__device__ __forceinline__ Fix96 to_fix_scaled(double v, int D) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m1 = (hi & 0xfffffu) | 0x100000u;
+  const int s = e - D - kFixE0;  // <= 31
+  Fix96 r;
+  if (e == 0) {
+    r = Fix96{0u, 0u, 0u};
+  } else if (s >= 0) {
+    r.w0 = lo << s;
+    r.w1 = __funnelshift_l(lo, m1, s);
+    r.w2 = __funnelshift_l(m1, 0u, s);
+  } else {
+    const int t = -s;
+    r.w0 = t < 32 ? __funnelshift_r(lo, m1, t) : (t < 53 ? m1 >> (t - 32) : 0u);
+    r.w1 = t < 32 ? m1 >> t : 0u;
+    r.w2 = 0u;
+  }
+  if (hi >> 31) r = fix_sub(Fix96{0u, 0u, 0u}, r);
+  return r;
+}
+
 // Exact conversion of a float32 with |v| < 4 (biased exponent <= 128):
 // v = M 2^(e - 150) for the 24-bit significand M, i.e. M shifted left by
 // e - 68 <= 60 places on the 2^-82 grid.  Values below 2^-58 keep their bits
@@ -163,8 +196,10 @@ __device__ __forceinline__ Fix96 to_fix_f32(float v, bool& ok) {
   return r;
 }
 
-// Round to the nearest float64 (ties to even).  The magnitude is below 2^95.
-__device__ __forceinline__ double fix_to_double(Fix96 a) {
+// Round a 2^D (a fixed-point value) to the nearest float64 (ties to even).
+// The magnitude is below 2^95; the caller keeps the result's exponent in
+// the normal range (D = 0 always does).
+__device__ __forceinline__ double fix_to_double_scaled(Fix96 a, int D) {
   const unsigned sign = a.w2 & 0x80000000u;
   if (sign) a = fix_sub(Fix96{0u, 0u, 0u}, a);
   if ((a.w0 | a.w1 | a.w2) == 0u) return 0.0;
@@ -195,8 +230,11 @@ __device__ __forceinline__ double fix_to_double(Fix96 a) {
   // value = m 2^(13 - lz - 52); the implicit bit of m adds one to the
   // exponent field, and a carry out of the rounding adds one more
   const unsigned long long bits =
-      ((unsigned long long)(13 - lz + 1022) << 52) + m + ((unsigned long long)sign << 32);
+      ((unsigned long long)(13 - lz + 1022 + D) << 52) + m + ((unsigned long long)sign << 32);
   return __longlong_as_double((long long)bits);
 }
+
+// Round to the nearest float64 (ties to even).  The magnitude is below 2^95.
+__device__ __forceinline__ double fix_to_double(Fix96 a) { return fix_to_double_scaled(a, 0); }
 
 }  // namespace lbm

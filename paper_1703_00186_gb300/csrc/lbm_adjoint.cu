@@ -70,8 +70,11 @@ __device__ __forceinline__ void push_cotangents(const double (&mu)[NPOP], int x,
   if (top) lam_out[scratch_idx(a, true, a.ly - 1 - y, x)] = wall_sum;
 }
 
+#ifndef LBM_ADJ_MINB
+#define LBM_ADJ_MINB 3  // minimum resident blocks per SM of the float64 adjoint step
+#endif
 template <int PREC>
-__global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restrict__ f_, const double* __restrict__ lam_in,
+__global__ void __launch_bounds__(ABX * ABY, LBM_ADJ_MINB) adjoint_kernel(const void* __restrict__ f_, const double* __restrict__ lam_in,
                                                             double* __restrict__ lam_out, LatticeArgs a) {
   using S = typename Dec<PREC>::T;
   const int x = blockIdx.x * ABX + threadIdx.x;
@@ -94,10 +97,16 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restri
   const double uys = sf.uy - a.tau_g_xi;
   const double v_x = a.r2 * sf.ux, v_y = a.r2 * uys;
   const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
-  double lam[NPOP];
+  // the cotangents wait in shared memory: the fixed-point sums and the
+  // relaxation read them twice, and registers hold the accumulators
+  __shared__ double s_lam[NPOP][ABX * ABY];
+  const int tid = threadIdx.y * ABX + threadIdx.x;
 #pragma unroll
-  for (int l = 0; l < NPOP; ++l) lam[l] = __ldg(lam_in + sidx(a, l, y, x));
-  const EqCot s = eq_cotangent_mono([&](int l) { return lam[l]; }, v_x, v_y, U2, theta, a);
+  for (int l = 0; l < NPOP; ++l) s_lam[l][tid] = __ldg(lam_in + sidx(a, l, y, x));
+  const auto lam = [&](int l) { return s_lam[l][tid]; };
+  double L[15];
+  if (!cotangent_moments_fix(lam, a, L)) cotangent_moments(lam, a, L);
+  const EqCot s = eq_cotangent_mono(L, v_x, v_y, U2, theta, a);
   // gamma_q = sum_m lam_m d f^eq_m / d q for q = rho, Jx, Jy, Exi (xi units)
   const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
   const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * v_x, s.SU, s.Scx));
@@ -109,13 +118,13 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_kernel(const void* __restri
   const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
   // mu_l = (1 - omega) lam_l + omega (gR + gJ . xi_l + gE |xi_l|^2)
   double mu[NPOP];
-  mu[0] = fma(a.omc, lam[0], wR);
+  mu[0] = fma(a.omc, lam(0), wR);
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) {
     const double base = fma(wE, (double)shell_sq(pair_shell(k)), wR);
     const double lin = pair_cu<double>(k, wJx, wJy);
-    mu[2 * k + 1] = fma(a.omc, lam[2 * k + 1], base + lin);
-    mu[2 * k + 2] = fma(a.omc, lam[2 * k + 2], base - lin);
+    mu[2 * k + 1] = fma(a.omc, lam(2 * k + 1), base + lin);
+    mu[2 * k + 2] = fma(a.omc, lam(2 * k + 2), base - lin);
   }
   push_cotangents(mu, x, y, a, lam_out);
 }

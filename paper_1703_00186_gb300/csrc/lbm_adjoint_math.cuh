@@ -158,16 +158,45 @@ __device__ __forceinline__ void cotangent_moments(GetLam lam, const LatticeArgs&
   L[14] = L14;
 }
 
+// The same 15 cotangent moments as exact fixed-point sums: the products
+// w_l lam_l (37 float64 multiplies) are put on the fixed-point grid with one
+// exponent D for the site, summed exactly with integer weights
+// (grouped_moments) and rounded once each.  D comes from a bound on the
+// largest product's exponent (that of lam_l plus that of w_l, plus one), so
+// the products are formed once, as the sums consume them.  Returns false,
+// having written nothing, where that bound leaves the range in which the
+// rounded sums are normal float64 numbers (products of 2^1010 and above,
+// nonzero products all below 2^-938, infinities, NaNs); the caller then takes
+// cotangent_moments.
+template <typename GetLam>
+__device__ __forceinline__ bool cotangent_moments_fix(GetLam lam, const LatticeArgs& a, double (&L)[15]) {
+  int ew[NSHELL];
+#pragma unroll
+  for (int j = 0; j < NSHELL; ++j) ew[j] = exp_field(a.w_shell[j]) - 1022;
+  int elam = exp_field(lam(0)), E = elam + ew[0];
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int ep = exp_field(lam(2 * k + 1)), em = exp_field(lam(2 * k + 2));
+    elam = max(elam, max(ep, em));
+    E = max(E, max(ep, em) + ew[pair_shell(k)]);
+  }
+  if (elam != 0 && (E < 84 || E > 2034)) return false;
+  const int D = elam != 0 ? E - kFixEMax : 0;  // every |w lam| 2^-D < 4
+  Fix96 n[15];
+  grouped_moments(
+      [&](int l) { return to_fix_scaled(a.w_shell[l == 0 ? 0 : pair_shell((l - 1) >> 1)] * lam(l), D); }, n);
+#pragma unroll
+  for (int i = 0; i < 15; ++i) L[i] = fix_to_double_scaled(n[i], D);
+  return true;
+}
+
 // The cotangent sums of eq_cotangent in monomial form: with the w-weighted
-// cotangent moments Lam_i = sum_l w_l lam_l xi_l^(c_i, e_i), every sum is a
+// cotangent moments L_i = sum_l w_l lam_l xi_l^(c_i, e_i), every sum is a
 // contraction of Lam with the monomial coefficients of the polynomial it sums
 // (P, dP/dU2, dP/dtheta, and P_cu times xi_x or xi_y, whose monomials are
 // those of P_cu shifted by one degree in x or y).
-template <typename GetLam>
-__device__ __forceinline__ EqCot eq_cotangent_mono(GetLam lam, double v_x, double v_y, double U2, double theta,
-                                                   const LatticeArgs& a) {
-  double L[15];
-  cotangent_moments(lam, a, L);
+__device__ __forceinline__ EqCot eq_cotangent_mono(const double (&L)[15], double v_x, double v_y, double U2,
+                                                   double theta, const LatticeArgs& a) {
   const EqCoef B = eq_coef(U2, theta);
   const double r2 = a.r2, r4 = r2 * r2;
   const double vx2 = v_x * v_x, vy2 = v_y * v_y, vxy = v_x * v_y;

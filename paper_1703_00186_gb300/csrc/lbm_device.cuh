@@ -895,10 +895,10 @@ __device__ __forceinline__ Fix96 fix_acc(Fix96 acc, Fix96 x, int k) {
 // Group {(A, B), (-A, B)}: pairs kp (A, B) and km (-A, B).  The axis pairs
 // (A, 0) and (0, B) come first, so S, T, U, V are already set; FIRST marks
 // the group (1, 1) that opens the six mixed moments.
-template <int A, int B, bool FIRST, typename F>
-__device__ __forceinline__ void reg_acc_diag(RegAcc& m, const F& f, int kp, int km, bool& ok) {
-  const Fix96 pp = to_fix(f(2 * kp + 1), ok), pm = to_fix(f(2 * kp + 2), ok);
-  const Fix96 mp = to_fix(f(2 * km + 1), ok), mm = to_fix(f(2 * km + 2), ok);
+template <int A, int B, bool FIRST, typename FX>
+__device__ __forceinline__ void reg_acc_diag(RegAcc& m, const FX& fx, int kp, int km) {
+  const Fix96 pp = fx(2 * kp + 1), pm = fx(2 * kp + 2);
+  const Fix96 mp = fx(2 * km + 1), mm = fx(2 * km + 2);
   const Fix96 sp = fix_add(pp, pm), sm = fix_add(mp, mm), dp = fix_sub(pp, pm), dm = fix_sub(mp, mm);
   const Fix96 Gs = fix_add(sp, sm), Hs = fix_sub(sp, sm), Gd = fix_add(dp, dm), Hd = fix_sub(dp, dm);
   m.S[A] = fix_add(m.S[A], Gs);
@@ -914,21 +914,57 @@ __device__ __forceinline__ void reg_acc_diag(RegAcc& m, const F& f, int kp, int 
 }
 
 // Pair (A, 0): opens S[A] and U[A].
-template <int A, typename F>
-__device__ __forceinline__ void reg_acc_axis_x(RegAcc& m, const F& f, int k, bool& ok) {
-  const Fix96 p = to_fix(f(2 * k + 1), ok), q = to_fix(f(2 * k + 2), ok);
+template <int A, typename FX>
+__device__ __forceinline__ void reg_acc_axis_x(RegAcc& m, const FX& fx, int k) {
+  const Fix96 p = fx(2 * k + 1), q = fx(2 * k + 2);
   m.S[A] = fix_add(p, q);
   m.U[A] = fix_sub(p, q);
 }
 
 // Pair (0, B): opens T[B] and V[B] (and Y with B = 1).
-template <int B, typename F>
-__device__ __forceinline__ void reg_acc_axis_y(RegAcc& m, const F& f, int k, bool& ok) {
-  const Fix96 p = to_fix(f(2 * k + 1), ok), q = to_fix(f(2 * k + 2), ok);
+template <int B, typename FX>
+__device__ __forceinline__ void reg_acc_axis_y(RegAcc& m, const FX& fx, int k) {
+  const Fix96 p = fx(2 * k + 1), q = fx(2 * k + 2);
   const Fix96 s = fix_add(p, q);
   m.T[B] = s;
   m.Y = B == 1 ? s : fix_add(m.Y, s);
   m.V[B] = fix_sub(p, q);
+}
+
+// The 15 monomial moments n_i = sum_l v_l xi_l^(c_i, e_i) (order of N) of
+// the fixed-point values fx(l), l = 0..36, as exact integer sums grouped per
+// axis pair and per group {(a, b), (-a, b)}.
+template <typename FX>
+__device__ __forceinline__ void grouped_moments(const FX& fx, Fix96 (&n)[15]) {
+  RegAcc m;
+  reg_acc_axis_x<1>(m, fx, 0);
+  reg_acc_axis_y<1>(m, fx, 1);
+  reg_acc_diag<1, 1, true>(m, fx, 2, 3);
+  reg_acc_axis_x<2>(m, fx, 4);
+  reg_acc_axis_y<2>(m, fx, 5);
+  reg_acc_diag<2, 1, false>(m, fx, 6, 9);
+  reg_acc_diag<1, 2, false>(m, fx, 7, 8);
+  reg_acc_diag<2, 2, false>(m, fx, 10, 11);
+  reg_acc_axis_x<3>(m, fx, 12);
+  reg_acc_axis_y<3>(m, fx, 13);
+  reg_acc_diag<3, 1, false>(m, fx, 14, 17);
+  reg_acc_diag<1, 3, false>(m, fx, 15, 16);
+  const Fix96 f0 = fx(0);
+  n[0] = fix_add(fix_add(f0, fix_add(m.S[1], m.S[2])), fix_add(m.S[3], m.Y));
+  n[1] = fix_mad(fix_mad(m.S[1], m.S[2], 4u), m.S[3], 9u);
+  n[2] = fix_mad(fix_mad(m.T[1], m.T[2], 4u), m.T[3], 9u);
+  n[3] = fix_mad(fix_mad(m.S[1], m.S[2], 16u), m.S[3], 81u);
+  n[4] = m.N22;
+  n[5] = fix_mad(fix_mad(m.T[1], m.T[2], 16u), m.T[3], 81u);
+  n[6] = fix_mad(fix_mad(m.U[1], m.U[2], 2u), m.U[3], 3u);
+  n[7] = fix_mad(fix_mad(m.U[1], m.U[2], 8u), m.U[3], 27u);
+  n[8] = m.N12;
+  n[9] = fix_mad(fix_mad(m.V[1], m.V[2], 2u), m.V[3], 3u);
+  n[10] = fix_mad(fix_mad(m.V[1], m.V[2], 8u), m.V[3], 27u);
+  n[11] = m.N21;
+  n[12] = m.N11;
+  n[13] = m.N31;
+  n[14] = m.N13;
 }
 
 // Fixed-point coefficients X of a polynomial in the monomials (order of N:
@@ -1017,35 +1053,10 @@ __device__ __forceinline__ void collide_fp64_reg_grouped(const double (&f_in)[NP
   bool ok = true;
   double N[15];
   {
-    RegAcc m;
-    reg_acc_axis_x<1>(m, f, 0, ok);
-    reg_acc_axis_y<1>(m, f, 1, ok);
-    reg_acc_diag<1, 1, true>(m, f, 2, 3, ok);
-    reg_acc_axis_x<2>(m, f, 4, ok);
-    reg_acc_axis_y<2>(m, f, 5, ok);
-    reg_acc_diag<2, 1, false>(m, f, 6, 9, ok);
-    reg_acc_diag<1, 2, false>(m, f, 7, 8, ok);
-    reg_acc_diag<2, 2, false>(m, f, 10, 11, ok);
-    reg_acc_axis_x<3>(m, f, 12, ok);
-    reg_acc_axis_y<3>(m, f, 13, ok);
-    reg_acc_diag<3, 1, false>(m, f, 14, 17, ok);
-    reg_acc_diag<1, 3, false>(m, f, 15, 16, ok);
-    const Fix96 f0 = to_fix(f(0), ok);
-    N[0] = fix_to_double(fix_add(fix_add(f0, fix_add(m.S[1], m.S[2])), fix_add(m.S[3], m.Y)));
-    N[1] = fix_to_double(fix_mad(fix_mad(m.S[1], m.S[2], 4u), m.S[3], 9u));
-    N[2] = fix_to_double(fix_mad(fix_mad(m.T[1], m.T[2], 4u), m.T[3], 9u));
-    N[3] = fix_to_double(fix_mad(fix_mad(m.S[1], m.S[2], 16u), m.S[3], 81u));
-    N[4] = fix_to_double(m.N22);
-    N[5] = fix_to_double(fix_mad(fix_mad(m.T[1], m.T[2], 16u), m.T[3], 81u));
-    N[6] = fix_to_double(fix_mad(fix_mad(m.U[1], m.U[2], 2u), m.U[3], 3u));
-    N[7] = fix_to_double(fix_mad(fix_mad(m.U[1], m.U[2], 8u), m.U[3], 27u));
-    N[8] = fix_to_double(m.N12);
-    N[9] = fix_to_double(fix_mad(fix_mad(m.V[1], m.V[2], 2u), m.V[3], 3u));
-    N[10] = fix_to_double(fix_mad(fix_mad(m.V[1], m.V[2], 8u), m.V[3], 27u));
-    N[11] = fix_to_double(m.N21);
-    N[12] = fix_to_double(m.N11);
-    N[13] = fix_to_double(m.N31);
-    N[14] = fix_to_double(m.N13);
+    Fix96 n[15];
+    grouped_moments([&](int l) { return to_fix(f(l), ok); }, n);
+#pragma unroll
+    for (int i = 0; i < 15; ++i) N[i] = fix_to_double(n[i]);
   }
   double Rv[15];
   if (ok) reg_coefficients(N, a, Rv);

@@ -63,6 +63,29 @@ def test_adjoint_step_parity(lx, ly, periodic_y, precision):
     assert plane_err(got, want) <= 1e-12
 
 
+@pytest.mark.parametrize("scale", [1e-200, 1e-30, 3.0, 1e150, 1e300, 1e-300])
+def test_adjoint_step_parity_at_any_cotangent_scale(scale):
+    # The float64 kernel sums the cotangents in block-scaled fixed point (one
+    # exponent per site): 1e300 sits near the top of its range, 1e-300 below
+    # it (those sites take the float64 sums).  Every scale meets the float64
+    # bar, and a power-of-two scale of the cotangents scales the result
+    # exactly.
+    lx, ly = 21, 9
+    p = M.Params(lx, ly, tau=0.7, g=2e-3, t_top=0.85, t_bottom=1.2)
+    f = noisy_state(lx, ly, 60)
+    lam = rand_cot(lx, ly, 61) * scale
+    lam[:, 3:-3][5, 4, 7] = 0.0                      # zero cotangents are exact
+    lam[:, 3:-3][:, 2, 3] = 0.0                      # a site with no cotangent at all
+    want = A.adjoint_step(f, lam, p)
+    lat = make(p)
+    got = lat.adjoint_step(to_dev(f), to_dev(lam)).cpu().numpy()
+    assert np.isfinite(M.physical(got)).all()
+    assert plane_err(got, want) <= 1e-12
+    if 1e-250 < scale < 1e250:                       # fixed-point path before and after
+        halved = lat.adjoint_step(to_dev(f), to_dev(lam * 2.0 ** -40)).cpu().numpy()
+        np.testing.assert_array_equal(M.physical(halved), M.physical(got) * 2.0 ** -40)
+
+
 def test_adjoint_step_fp32_state_parity():
     lx, ly = 16, 12
     rho0 = 1.05
