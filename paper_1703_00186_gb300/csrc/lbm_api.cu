@@ -149,9 +149,12 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
     a->c4e_shell[j] = 0.125 * (q->c2_shell[j] * q->c2_shell[j]);
     a->w6_shell[j] = q->w_shell[j] / 6.0;
   }
-  if (a->regularized && regularization_gram_inverse(*q, a->ginv) != 0) {
-    std::snprintf(err, errlen, "singular Gram matrix");
-    return LBM_ERR_INVALID;
+  if (a->regularized) {
+    if (regularization_gram_inverse(*q, a->ginv) != 0) {
+      std::snprintf(err, errlen, "singular Gram matrix");
+      return LBM_ERR_INVALID;
+    }
+    for (double& g : a->ginv) g *= a->omc;  // the collide only needs (1 - omega) G^-1
   }
   wall_ratios(*q, p.t_bottom, 0, a->q_bot);
   wall_ratios(*q, p.t_top, 1, a->q_top);

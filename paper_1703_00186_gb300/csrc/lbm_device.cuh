@@ -786,7 +786,8 @@ __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const La
   const double P00 = Pm[0], P20 = Pm[1], P02 = Pm[2], P40 = Pm[3], P22 = Pm[4], P04 = Pm[5];
   const double P10 = Pm[6], P30 = Pm[7], P12 = Pm[8], P01 = Pm[9], P03 = Pm[10], P21 = Pm[11];
   const double P11 = Pm[12], P31 = Pm[13], P13 = Pm[14];
-  // projection coefficients q = G^-1 N, block by block
+  // relaxed projection coefficients (1 - omega) q = (1 - omega) G^-1 N, block
+  // by block (the lattice constants hold (1 - omega) G^-1)
   const double* G = a.ginv;
   const double NE[6] = {N00, N20, N02, N40, N22, N04};
   double q[6];
@@ -806,12 +807,12 @@ __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const La
   blk3(45, N01, N03, N21, qeo);
   blk3(54, N11, N31, N13, qoo);
   // R = omega rho P + (1 - omega) q
-  const double wr = a.omega * sf.rho, om = a.omc;
-  const double R00 = fma(wr, P00, om * q[0]), R20 = fma(wr, P20, om * q[1]), R02 = fma(wr, P02, om * q[2]);
-  const double R40 = fma(wr, P40, om * q[3]), R22 = fma(wr, P22, om * q[4]), R04 = fma(wr, P04, om * q[5]);
-  const double R10 = fma(wr, P10, om * qoe[0]), R30 = fma(wr, P30, om * qoe[1]), R12 = fma(wr, P12, om * qoe[2]);
-  const double R01 = fma(wr, P01, om * qeo[0]), R03 = fma(wr, P03, om * qeo[1]), R21 = fma(wr, P21, om * qeo[2]);
-  const double R11 = fma(wr, P11, om * qoo[0]), R31 = fma(wr, P31, om * qoo[1]), R13 = fma(wr, P13, om * qoo[2]);
+  const double wr = a.omega * sf.rho;
+  const double R00 = fma(wr, P00, q[0]), R20 = fma(wr, P20, q[1]), R02 = fma(wr, P02, q[2]);
+  const double R40 = fma(wr, P40, q[3]), R22 = fma(wr, P22, q[4]), R04 = fma(wr, P04, q[5]);
+  const double R10 = fma(wr, P10, qoe[0]), R30 = fma(wr, P30, qoe[1]), R12 = fma(wr, P12, qoe[2]);
+  const double R01 = fma(wr, P01, qeo[0]), R03 = fma(wr, P03, qeo[1]), R21 = fma(wr, P21, qeo[2]);
+  const double R11 = fma(wr, P11, qoo[0]), R31 = fma(wr, P31, qoo[1]), R13 = fma(wr, P13, qoo[2]);
   Rv[0] = R00; Rv[1] = R20; Rv[2] = R02; Rv[3] = R40; Rv[4] = R22; Rv[5] = R04;
   Rv[6] = R10; Rv[7] = R30; Rv[8] = R12; Rv[9] = R01; Rv[10] = R03; Rv[11] = R21;
   Rv[12] = R11; Rv[13] = R31; Rv[14] = R13;

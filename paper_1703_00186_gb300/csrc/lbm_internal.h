@@ -108,7 +108,7 @@ struct LatticeArgs {
   float df_omc[2];        // 1 - omega
   float df_w_shell[NSHELL][2];
   int regularized;        // LBM_FLAG_REGULARIZED
-  double ginv[63];        // inverse Gram blocks EE(36) OE(9) EO(9) OO(9)
+  double ginv[63];        // (1 - omega) x inverse Gram blocks EE(36) OE(9) EO(9) OO(9)
   float df_c2_shell[NSHELL][2];
   unsigned int* status;  // device status word
   // Site-relative offsets for states of fewer than 2^31 elements
