@@ -311,6 +311,34 @@ def test_one_step_parity_regularized(lx, ly, periodic_y):
     assert plane_err(lat.state().cpu().numpy(), want) <= 1e-12
 
 
+def test_one_step_parity_bgk_outside_the_fixed_point_range():
+    # The float64 BGK collide evaluates the equilibrium polynomial in fixed
+    # point; a site whose equilibrium coefficients leave their degree-graded
+    # range (a very hot or very fast site) relaxes in float64 instead, and a
+    # population >= 4 sends the moment sums to float64.  All paths match the
+    # oracle.
+    lx, ly = 37, 11
+    p = M.Params(lx, ly, tau=0.7, g=1e-3, t_top=0.9, t_bottom=1.1)
+    rho, ux, uy, T = synth.random_fields(lx, ly, 433, umax=0.08)
+    T[2, 7] = 60.0                                         # theta^2 terms beyond 2^10
+    ux[6, 12] = 3.0                                        # degree-4 velocity terms beyond 2^2
+    rho[4, 25] = 30.0                                      # populations >= 4, coefficients in range
+    f = M.init_state(rho, ux, uy, T)
+    f[:, 3:-3] *= 1.0 + 0.02 * synth.noise(lx, ly, 434)
+    phys = f[:, 3:-3]
+    phys[21, 1, 3] = 0.0
+    phys[30, 8, 33] = 1e-300
+    want = M.physical(M.step(f, p))
+    lat = make(p)
+    lat.set_state(to_dev(f))
+    lat.step(1)
+    got = M.physical(lat.state().cpu().numpy())
+    # per site: the hot site's populations (~500) would hide errors elsewhere
+    # in a per-plane scale
+    site_err = np.abs(got - want).max(axis=0) / np.abs(want).max(axis=0)
+    assert site_err.max() <= 1e-12
+
+
 def test_one_step_parity_regularized_outside_the_fixed_point_range():
     # Sites whose pulled populations include one >= 4 (or whose projection
     # coefficients leave the fixed-point range) relax in float64; tiny, zero
