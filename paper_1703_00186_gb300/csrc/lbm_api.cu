@@ -137,6 +137,10 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->omc = 1.0 - a->omega;
   a->r = q->r;
   a->r2 = q->r * q->r;
+  a->r2_2 = 0.5 * a->r2;
+  a->r2_4 = 0.25 * a->r2;
+  a->r4_4 = 0.25 * (a->r2 * a->r2);
+  a->r4_8 = 0.125 * (a->r2 * a->r2);
   a->inv_r2 = q->y;
   a->tau_g_xi = p.tau * p.g / q->r;
   a->tshift = p.tau * (1.0 - p.tau) * p.g * p.g / 2.0 - 1.0;

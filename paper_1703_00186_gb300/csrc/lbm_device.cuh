@@ -744,28 +744,33 @@ __device__ __forceinline__ void eq_monomials(const SiteFields& sf, const Lattice
   const double uys = sf.uy - a.tau_g_xi;
   const double vx_ = a.r2 * sf.ux, vy_ = a.r2 * uys;
   const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
-  const EqCoef B = eq_coef(U2, theta);
-  // equilibrium polynomial P in the monomials (cu = xi . v, c2 = r^2 |xi|^2)
-  const double r2 = a.r2, r4 = r2 * r2;
+  // the Hermite coefficients of eq_coef that enter without a theta multiple
+  // (B11 r^2 = theta r^2 / 2, B21 r^2 = theta r^2 / 4 and B02 r^4 = theta^2
+  // r^4 / 8 use the lattice's multiples of r^2 and r^4)
+  const double h = fma(-0.25, U2, 0.5);
+  const double B20 = fma(-1.5, theta, h);
+  const double B10 = fma(-2.0, theta, fma(-0.5, U2, 1.0));
+  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(U2, fma(0.125, U2, -0.5), 1.0));
+  const double B01r2 = (theta * a.r2) * (h - theta);
+  const double th2 = theta * theta;
+  const double t4 = theta * a.r2_4, t2 = theta * a.r2_2;
   const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
-  const double P00 = B.B00;
-  const double P20 = fma(B.B01, r2, B.B20 * vx2);
-  const double P02 = fma(B.B01, r2, B.B20 * vy2);
-  const double P11 = 2.0 * B.B20 * vxy;
-  const double P40 = fma(B.B02, r4, fma(B.B21 * r2, vx2, vx2 * vx2 * (1.0 / 24.0)));
-  const double P04 = fma(B.B02, r4, fma(B.B21 * r2, vy2, vy2 * vy2 * (1.0 / 24.0)));
-  const double P22 = fma(2.0 * B.B02, r4, fma(B.B21 * r2, vx2 + vy2, vx2 * vy2 * 0.25));
-  const double P31 = vxy * fma(2.0 * B.B21, r2, vx2 * (1.0 / 6.0));
-  const double P13 = vxy * fma(2.0 * B.B21, r2, vy2 * (1.0 / 6.0));
-  const double P10 = B.B10 * vx_;
-  const double P01 = B.B10 * vy_;
-  const double P30 = vx_ * fma(B.B11, r2, vx2 * (1.0 / 6.0));
-  const double P03 = vy_ * fma(B.B11, r2, vy2 * (1.0 / 6.0));
-  const double P21 = vy_ * fma(B.B11, r2, vx2 * 0.5);
-  const double P12 = vx_ * fma(B.B11, r2, vy2 * 0.5);
-  P[0] = P00; P[1] = P20; P[2] = P02; P[3] = P40; P[4] = P22; P[5] = P04;
-  P[6] = P10; P[7] = P30; P[8] = P12; P[9] = P01; P[10] = P03; P[11] = P21;
-  P[12] = P11; P[13] = P31; P[14] = P13;
+  const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);  // B11 r^2 + v^2 / 6
+  P[0] = B00;
+  P[1] = fma(B20, vx2, B01r2);
+  P[2] = fma(B20, vy2, B01r2);
+  P[3] = fma(th2, a.r4_8, vx2 * fma(vx2, 1.0 / 24.0, t4));
+  P[4] = fma(th2, a.r4_4, fma(t4, vx2 + vy2, 0.25 * (vx2 * vy2)));
+  P[5] = fma(th2, a.r4_8, vy2 * fma(vy2, 1.0 / 24.0, t4));
+  P[6] = B10 * vx_;
+  P[7] = vx_ * I;
+  P[8] = vx_ * fma(0.5, vy2, t2);
+  P[9] = B10 * vy_;
+  P[10] = vy_ * J;
+  P[11] = vy_ * fma(0.5, vx2, t2);
+  P[12] = (B20 + B20) * vxy;
+  P[13] = vxy * I;
+  P[14] = vxy * J;
 }
 
 // The regularised collide's coefficients R of the new populations
@@ -1082,7 +1087,7 @@ __device__ __forceinline__ void collide_fp64_reg_grouped(const double (&f_in)[NP
 // evaluates population by population in float64).  The moments are the exact
 // fixed-point sums of site_moments; P(xi_l) is an exact fixed-point sum of its
 // 15 coefficients with integer weights, rounded once; float64 does the site
-// fields, the coefficients, the eight shell factors omega rho w_j and one
+// fields, the coefficients, the eight shell factors rho (omega w_j) and one
 // multiply and one fused multiply-add per population.  The populations wait in
 // shared memory (s_f[l][tid]) for the relaxation.  Sites with a coefficient
 // outside poly_to_fix's range take collide_fp64.
@@ -1108,10 +1113,9 @@ __device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], 
     for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
     return sf;
   }
-  const double wr = a.omega * sf.rho;
-  double sw[NSHELL];
+  double sw[NSHELL];  // omega rho w_j
 #pragma unroll
-  for (int j = 0; j < NSHELL; ++j) sw[j] = wr * a.w_shell[j];
+  for (int j = 0; j < NSHELL; ++j) sw[j] = sf.rho * a.ow_shell[j];
   dst[sidx(a, 0, y, x)] = fma(a.omc, s_f[0][tid], sw[0] * P[0]);
   poly_eval_grouped(X, [&](int k, Fix96 ev, Fix96 od) {
     const double w = sw[pair_shell(k)];
