@@ -351,7 +351,7 @@ def rollout_study(steps, torch):
     forward rollout and of the backward sweep (recompute + adjoint steps),
     and the gradient against float64 central differences on 16 seeded
     directions; FP64, FP32-store and FP64_DF (double-float collide and
-    cotangent sums)."""
+    cotangent sums), and the FP32-store rollout with float32 cotangents."""
     import numpy as np
 
     import synth
@@ -366,23 +366,27 @@ def rollout_study(steps, torch):
     res = {"lattice": f"{lx}x{ly}", "steps": steps, "checkpoint_every": K, "tau": tau, "g": g}
     grads = {}
     fds, dirs = [], []
-    for prec in ("fp64", "fp32", "fp64df"):
+    # "fp32_f32cot": the FP32-store rollout with float32 cotangents and the
+    # float32 adjoint (lbm_adjoint_step_f32)
+    for name in ("fp64", "fp32", "fp64df", "fp32_f32cot"):
+        prec = "fp32" if name == "fp32_f32cot" else name
+        cot = torch.float32 if name == "fp32_f32cot" else torch.float64
         lat = Lattice(lx, ly, tau=tau, g=g, t_top=tt, t_bottom=tb, precision=prec, rho0=float(rho.mean()))
         d = torch.tensor(dT0, device=dev, requires_grad=True)
-        temperature_loss(d, lat, rho_t, T_t, tgt, 4, 2).backward()  # warm-up
+        temperature_loss(d, lat, rho_t, T_t, tgt, 4, 2, cotangent_dtype=cot).backward()  # warm-up
         d.grad = None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        J = temperature_loss(d, lat, rho_t, T_t, tgt, steps, K)
+        J = temperature_loss(d, lat, rho_t, T_t, tgt, steps, K, cotangent_dtype=cot)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         J.backward()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        grads[prec] = d.grad.detach().cpu().numpy()
-        res[prec] = {"J": float(J.detach()), "forward_s": t1 - t0, "backward_s": t2 - t1,
+        grads[name] = d.grad.detach().cpu().numpy()
+        res[name] = {"J": float(J.detach()), "forward_s": t1 - t0, "backward_s": t2 - t1,
                      "backward_over_forward": (t2 - t1) / (t1 - t0)}
-        if prec == "fp64":
+        if name == "fp64":
             # float64 central differences of the float64 rollout on 16 seeded
             # directions: the check of every variant's gradient
             rng = np.random.default_rng(2024)
@@ -398,14 +402,14 @@ def rollout_study(steps, torch):
                 fds.append((jp - jm) / (2 * eps))
             res["fd_eps"] = eps
             res["fd_of"] = "float64 central differences of the float64 rollout, 16 seeded directions"
-        errs = [abs(fd - float((grads[prec] * v).sum())) / abs(fd) for fd, v in zip(fds, dirs)]
-        res[prec]["fd_max_rel_err_16_dirs"] = max(errs)
-        res[prec]["fd_pass_1e-6"] = max(errs) <= 1e-6
+        errs = [abs(fd - float((grads[name] * v).sum())) / abs(fd) for fd, v in zip(fds, dirs)]
+        res[name]["fd_max_rel_err_16_dirs"] = max(errs)
+        res[name]["fd_pass_1e-6"] = max(errs) <= 1e-6
         del lat
         torch.cuda.empty_cache()
     g64 = grads["fp64"]
-    for prec in ("fp32", "fp64df"):
-        res[prec]["grad_rel_diff_vs_fp64"] = float(np.abs(grads[prec] - g64).max() / np.abs(g64).max())
+    for name in ("fp32", "fp64df", "fp32_f32cot"):
+        res[name]["grad_rel_diff_vs_fp64"] = float(np.abs(grads[name] - g64).max() / np.abs(g64).max())
     res["fp64df"]["backward_over_fp64_forward"] = res["fp64df"]["backward_s"] / res["fp64"]["forward_s"]
     return res
 
@@ -610,12 +614,12 @@ def main():
         del lat
         torch.cuda.empty_cache()
     if "adjoint" in only:
-        def adjoint_times(precision):
+        def adjoint_times(precision, cot=torch.float64):
             lat, _ = rt_lattice(lx, ly, precision)
             lat.step(W)
             f_t = lat.state().clone()
-            lam_a = lat.new_cotangent(0.0).normal_()
-            lam_b = lat.new_cotangent(0.0)
+            lam_a = lat.new_cotangent(0.0, dtype=cot).normal_()
+            lam_b = lat.new_cotangent(0.0, dtype=cot)
             ka = max(3, K // 4)
             for _ in range(2):
                 lat.adjoint_step(f_t, lam_a, lam_b)
@@ -643,6 +647,13 @@ def main():
         ta_df, tf_df = adjoint_times("fp64df")
         out["adjoint"]["fp64df"] = {"adjoint_ms_per_step": ta_df, "forward_ms_per_step": tf_df,
                                     "ratio": ta_df / tf_df, "ratio_vs_fp64_forward": ta_df / tf_ms}
+        # FP32-store: float64 cotangents (double-float sums) and float32
+        # cotangents (lbm_adjoint_step_f32)
+        ta32, tf32 = adjoint_times("fp32")
+        ta32f, _ = adjoint_times("fp32", torch.float32)
+        out["adjoint"]["fp32"] = {"adjoint_ms_per_step": ta32, "forward_ms_per_step": tf32, "ratio": ta32 / tf32,
+                                  "f32_cotangents": {"adjoint_ms_per_step": ta32f, "ratio": ta32f / tf32,
+                                                     "hbm_gbs": 3 * 37 * 4 * sites / (ta32f * 1e-3) / 1e9}}
     if "e2e" in only:
         # Independent lattices, each on its own stream, each step of each
         # lattice through the C ABI from and to pinned host memory:

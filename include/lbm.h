@@ -340,6 +340,33 @@ int lbm_init_vjp(lbm_ctx* ctx, const double* rho, const double* ux,
                  const double* uy, const double* T, const double* lam,
                  double* g_rho, double* g_ux, double* g_uy, double* g_T);
 
+/* Float32 cotangents for LBM_FP32_SHIFTED contexts.  The paper has no
+ * counterpart of these calls: they make the discrete adjoint of the FP32-store
+ * step as cheap as its storage allows.
+ *
+ * lbm_adjoint_step_f32: lam_out = P^T B^T C^T lam_in as lbm_adjoint_step, with
+ * lam_in and lam_out float arrays in the FP32 state layout (37 planes of
+ * (ly + 6) x lx, must not alias).  The site fields of f_t are formed as in
+ * lbm_adjoint_step (exact moment sums, float64 rho, u, T) and rounded to
+ * float32; every cotangent sum, the relaxation of the cotangents and the
+ * transposed walls run in float32, so a result is within a few float32
+ * roundings (relative 1e-6 of the site's largest cotangent) of the float64
+ * adjoint of the decoded state.  The halo rows of lam_out are used as scratch
+ * and hold no data afterwards.  LBM_ERR_INVALID for a context of another
+ * precision or for bad buffers.
+ *
+ * lbm_moments_vjp_f32, lbm_init_vjp_f32: lbm_moments_vjp with a float32
+ * lam_out (computed in float64, rounded once), and lbm_init_vjp reading a
+ * float32 lam; any precision. */
+int lbm_adjoint_step_f32(lbm_ctx* ctx, const void* f_t, const float* lam_in,
+                         float* lam_out);
+int lbm_moments_vjp_f32(lbm_ctx* ctx, const void* f, const double* g_rho,
+                        const double* g_ux, const double* g_uy,
+                        const double* g_T, float* lam_out);
+int lbm_init_vjp_f32(lbm_ctx* ctx, const double* rho, const double* ux,
+                     const double* uy, const double* T, const float* lam,
+                     double* g_rho, double* g_ux, double* g_uy, double* g_T);
+
 /* Check that every physical population of state f (NULL = current) is
  * finite.  Synchronises the stream; *ok = 1 if finite, else 0. */
 int lbm_check_finite(lbm_ctx* ctx, const void* f, int* ok);

@@ -82,6 +82,9 @@ SIGNATURES = {
     "lbm_adjoint_step_noalloc": (c_int, [P(LbmParams), c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_moments_vjp": (c_int, [c_void_p] * 7),
     "lbm_init_vjp": (c_int, [c_void_p] * 10),
+    "lbm_adjoint_step_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_moments_vjp_f32": (c_int, [c_void_p] * 7),
+    "lbm_init_vjp_f32": (c_int, [c_void_p] * 10),
     "lbm_check_finite": (c_int, [c_void_p, c_void_p, P(c_int)]),
     "lbm_status": (c_int, [c_void_p]),
     "lbm_constants": (c_int, [c_void_p, P(c_double), P(c_double), P(c_double), P(c_double)]),

@@ -23,7 +23,7 @@ class TemperatureRollout(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, dT0: torch.Tensor, lattice: Lattice, rho0: torch.Tensor, T0: torch.Tensor,
-                n: int, K: int):
+                n: int, K: int, cotangent_dtype: torch.dtype = torch.float64):
         lat = lattice
         z = torch.zeros_like(rho0)
         Tin = (T0 + dT0.detach()).contiguous()
@@ -39,6 +39,7 @@ class TemperatureRollout(torch.autograd.Function):
         T_n = lat.moments(f_n)[3]
         ctx.lattice = lat
         ctx.n, ctx.K = n, K
+        ctx.cot = cotangent_dtype
         ctx.ckpts = ckpts
         ctx.save_for_backward(rho0, Tin, f_n)
         return T_n
@@ -48,8 +49,8 @@ class TemperatureRollout(torch.autograd.Function):
         lat: Lattice = ctx.lattice
         rho0, Tin, f_n = ctx.saved_tensors
         n, K = ctx.n, ctx.K
-        lam = lat.moments_vjp(f_n, None, None, None, gT.contiguous())
-        lam_next = lat.new_cotangent()
+        lam = lat.moments_vjp(f_n, None, None, None, gT.contiguous(), dtype=ctx.cot)
+        lam_next = lat.new_cotangent(dtype=ctx.cot)
         seg_states = [lat.new_state() for _ in range(K)]
         nseg = len(ctx.ckpts)
         for s in range(nseg - 1, -1, -1):
@@ -63,11 +64,14 @@ class TemperatureRollout(torch.autograd.Function):
         z = torch.zeros_like(rho0)
         g = lat.init_vjp(rho0, z, z, Tin, lam)[3]
         ctx.ckpts = None
-        return g, None, None, None, None, None
+        return g, None, None, None, None, None, None
 
 
-def temperature_loss(dT0, lattice: Lattice, rho0, T0, T_target, n: int, K: int = 50):
-    """J = mean over sites of (T_n - T_target)^2, differentiable in dT0."""
-    T_n = TemperatureRollout.apply(dT0, lattice, rho0, T0, n, K)
+def temperature_loss(dT0, lattice: Lattice, rho0, T0, T_target, n: int, K: int = 50,
+                     cotangent_dtype: torch.dtype = torch.float64):
+    """J = mean over sites of (T_n - T_target)^2, differentiable in dT0.
+    cotangent_dtype=torch.float32 runs the backward sweep with float32
+    cotangents and the float32 adjoint (FP32-store lattices only)."""
+    T_n = TemperatureRollout.apply(dT0, lattice, rho0, T0, n, K, cotangent_dtype)
     d = T_n - T_target
     return (d * d).mean()

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_adjoint_math.cuh"
+#include "lbm_adjoint_f32.cuh"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -46,11 +47,14 @@ __device__ __forceinline__ long long scratch_idx(const LatticeArgs& a, bool top,
 
 // P^T: push each cotangent back to its pull source; the cotangents of wall
 // slots (filled by bc with M(x) q_l) reduce into lam_out's halo-row scratch.
-__device__ __forceinline__ void push_cotangents(const double (&mu)[NPOP], int x, int y, const LatticeArgs& a,
-                                                double* __restrict__ lam_out) {
+// R is the cotangents' storage type (double, or float for
+// lbm_adjoint_step_f32).
+template <typename R>
+__device__ __forceinline__ void push_cotangents(const R (&mu)[NPOP], int x, int y, const LatticeArgs& a,
+                                                R* __restrict__ lam_out) {
   const bool bottom = !a.periodic_y && y < 3;
   const bool top = !a.periodic_y && y >= a.ly - 3;
-  double wall_sum = 0.0;
+  R wall_sum = R(0);
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) {
     int ys = y - vy(l);
@@ -63,7 +67,7 @@ __device__ __forceinline__ void push_cotangents(const double (&mu)[NPOP], int x,
     if (known) {
       lam_out[sidx(a, l, ys, wrap_x(x - vx(l), a.lx))] = mu[l];
     } else {
-      wall_sum = fma(ys < 0 ? a.q_bot[l] : a.q_top[l], mu[l], wall_sum);
+      wall_sum = fma(R(ys < 0 ? a.q_bot[l] : a.q_top[l]), mu[l], wall_sum);
     }
   }
   if (bottom) lam_out[scratch_idx(a, false, y, x)] = wall_sum;
@@ -292,15 +296,16 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const void* __res
 // B^T for the populations that left through a wall: lam_out(l, y0, x) =
 // Lambda(x + xi_lx), Lambda(x) = sum over the three wall rows of the partial
 // sums written by adjoint_kernel.
-__global__ void walls_adjoint_kernel(double* __restrict__ lam_out, LatticeArgs a) {
+template <typename R>
+__global__ void walls_adjoint_kernel(R* __restrict__ lam_out, LatticeArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool top = blockIdx.y == 1;
   if (x >= a.lx) return;
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) {
     const int xl = wrap_x(x + vx(l), a.lx);
-    const double Lam = (lam_out[scratch_idx(a, top, 0, xl)] + lam_out[scratch_idx(a, top, 1, xl)]) +
-                       lam_out[scratch_idx(a, top, 2, xl)];
+    const R Lam = (lam_out[scratch_idx(a, top, 0, xl)] + lam_out[scratch_idx(a, top, 1, xl)]) +
+                  lam_out[scratch_idx(a, top, 2, xl)];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       if (!top && e + vy(l) < 0) lam_out[sidx(a, l, e, x)] = Lam;
@@ -312,12 +317,12 @@ __global__ void walls_adjoint_kernel(double* __restrict__ lam_out, LatticeArgs a
 // lam_l = g_rho d rho/d f_l + g_u . d u/d f_l + g_T d T/d f_l  (eq. 2):
 //   d rho/d f_l = 1, d u/d f_l = (c_l - u) / rho,
 //   d T/d f_l = (|c_l - u|^2 - D T) / (D rho).
-template <int PREC>
+template <int PREC, typename R>
 __global__ void __launch_bounds__(ABX * ABY) moments_vjp_kernel(const void* __restrict__ f_, const double* __restrict__ g_rho,
                                                                 const double* __restrict__ g_ux,
                                                                 const double* __restrict__ g_uy,
                                                                 const double* __restrict__ g_T,
-                                                                double* __restrict__ lam_out, LatticeArgs a) {
+                                                                R* __restrict__ lam_out, LatticeArgs a) {
   using S = typename Dec<PREC>::T;
   const int x = blockIdx.x * ABX + threadIdx.x;
   const int y = blockIdx.y * ABY + threadIdx.y;
@@ -337,14 +342,15 @@ __global__ void __launch_bounds__(ABX * ABY) moments_vjp_kernel(const void* __re
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) {
     const double dx = vx(l) - sf.ux, dy = vy(l) - sf.uy;
-    lam_out[sidx(a, l, y, x)] = fma(kt, fma(dx, dx, dy * dy), fma(ku, fma(gx, dx, gy * dy), base));
+    lam_out[sidx(a, l, y, x)] = R(fma(kt, fma(dx, dx, dy * dy), fma(ku, fma(gx, dx, gy * dy), base)));
   }
 }
 
 // g_q = sum_l lam_l d f^eq_l(rho, u, T) / d q for q = rho, ux, uy, T.
+template <typename R>
 __global__ void __launch_bounds__(ABX * ABY) init_vjp_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
                                                              const double* __restrict__ uy, const double* __restrict__ T,
-                                                             const double* __restrict__ lam, double* __restrict__ g_rho,
+                                                             const R* __restrict__ lam, double* __restrict__ g_rho,
                                                              double* __restrict__ g_ux, double* __restrict__ g_uy,
                                                              double* __restrict__ g_T, LatticeArgs a) {
   const int x = blockIdx.x * ABX + threadIdx.x;
@@ -353,12 +359,75 @@ __global__ void __launch_bounds__(ABX * ABY) init_vjp_kernel(const double* __res
   const long long i = (long long)y * a.lx + x;
   const double r0 = rho[i], u0 = ux[i], u1 = uy[i];
   const double U2 = fma(u0, u0, u1 * u1);
-  const EqCot s = eq_cotangent([&](int l) { return __ldg(lam + sidx(a, l, y, x)); }, a.r * u0, a.r * u1, U2,
+  const EqCot s = eq_cotangent([&](int l) { return (double)__ldg(lam + sidx(a, l, y, x)); }, a.r * u0, a.r * u1, U2,
                                T[i] - 1.0, a);
   if (g_rho) g_rho[i] = s.SP;
   if (g_ux) g_ux[i] = r0 * fma(a.r, s.Scx, 2.0 * u0 * s.SU);
   if (g_uy) g_uy[i] = r0 * fma(a.r, s.Scy, 2.0 * u1 * s.SU);
   if (g_T) g_T[i] = r0 * s.Sth;
+}
+
+// Adjoint step of FP32-store contexts with float32 cotangents
+// (lbm_adjoint_step_f32): the transposed Jacobian of adjoint_kernel with the
+// cotangents read, summed, relaxed and pushed in float32 (FP32 pipe).  The
+// site fields of the forward state are exact fixed-point moment sums of the
+// float32 deviations (away from the walls) and float64 fields, rounded once
+// to float32.  Per site it moves 148 B of state and 2 x 148 B of cotangents.
+__global__ void __launch_bounds__(ABX * ABY) adjoint_f32_kernel(const float* __restrict__ src,
+                                                                const float* __restrict__ lam_in,
+                                                                float* __restrict__ lam_out, LatticeArgs a) {
+  const int x = blockIdx.x * ABX + threadIdx.x;
+  const int y = blockIdx.y * ABY + threadIdx.y;
+  if (x >= a.lx || y >= a.ly) return;
+  Dec<LBM_FP32_SHIFTED> dec{&a};
+  SiteFields sf;
+  {
+    float g[NPOP];
+    pull(src, x, y, a, g);
+    Moments mo;
+    bool exact = false;
+    if (a.periodic_y || (y >= 3 && y < a.ly - 3)) exact = moment_sums_f32_exact(g, a, mo);
+    if (!exact) {
+      double f[NPOP];
+#pragma unroll
+      for (int l = 0; l < NPOP; ++l) f[l] = dec(l, g[l]);
+      walls(src, x, y, a, f, dec, [](int, double v) { return v; });
+      mo = site_moments([&](int l) { return f[l]; });
+    }
+    sf = site_fields(mo, a);
+  }
+  float lam[NPOP];
+#pragma unroll
+  for (int l = 0; l < NPOP; ++l) lam[l] = __ldg(lam_in + sidx(a, l, y, x));
+  float L[15];
+  cotangent_moments_f(lam, a, L);
+  const float ux = (float)sf.ux, uy = (float)sf.uy, T = (float)sf.T;
+  const float theta = (float)(sf.T + a.tshift), uys = (float)(sf.uy - a.tau_g_xi);
+  const float r2 = a.df_r2[0], ir2 = a.df_inv_r2[0];
+  const float v_x = r2 * ux, v_y = r2 * uys;
+  const float U2 = r2 * fmaf(ux, ux, uys * uys);
+  const EqCotF s = eq_cotangent_mono_f(L, v_x, v_y, U2, theta, a);
+  // gamma_q = sum_m lam_m d f^eq_m / d q for q = rho, Jx, Jy, Exi (xi units)
+  const float usq = fmaf(ux, ux, uy * uy);
+  const float kx = 2.0f * ir2 * v_x, ky = 2.0f * ir2 * v_y;
+  const float gJx = r2 * fmaf(-s.Sth, ux, fmaf(kx, s.SU, s.Scx));
+  const float gJy = r2 * fmaf(-s.Sth, uy, fmaf(ky, s.SU, s.Scy));
+  const float gE = 0.5f * r2 * s.Sth;
+  const float gR = s.SP - r2 * (ux * fmaf(kx, s.SU, s.Scx) + uy * fmaf(ky, s.SU, s.Scy)) +
+                   s.Sth * fmaf(0.5f * r2, usq, -T);
+  const float om = a.omega_f, omc = a.omc_f;
+  const float wR = om * gR, wJx = om * gJx, wJy = om * gJy, wE = om * gE;
+  // mu_l = (1 - omega) lam_l + omega (gR + gJ . xi_l + gE |xi_l|^2)
+  float mu[NPOP];
+  mu[0] = fmaf(omc, lam[0], wR);
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const float base = fmaf(wE, (float)shell_sq(pair_shell(k)), wR);
+    const float lin = pair_cu<float>(k, wJx, wJy);
+    mu[2 * k + 1] = fmaf(omc, lam[2 * k + 1], base + lin);
+    mu[2 * k + 2] = fmaf(omc, lam[2 * k + 2], base - lin);
+  }
+  push_cotangents(mu, x, y, a, lam_out);
 }
 
 static dim3 site_grid(const LatticeArgs& a) {
@@ -380,19 +449,47 @@ cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux, const double* g_uy,
-                               const double* g_T, double* lam_out, const LatticeArgs& a, cudaStream_t s) {
+cudaError_t launch_adjoint_f32(const void* f_t, const float* lam_in, float* lam_out, const LatticeArgs& a,
+                               cudaStream_t s) {
+  adjoint_f32_kernel<<<site_grid(a), dim3(ABX, ABY), 0, s>>>(static_cast<const float*>(f_t), lam_in, lam_out, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.periodic_y) return e;
+  walls_adjoint_kernel<<<dim3((unsigned)((a.lx + 127) / 128), 2), 128, 0, s>>>(lam_out, a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_moments_vjp_t(int prec, const void* f, const double* g_rho, const double* g_ux, const double* g_uy,
+                                 const double* g_T, R* lam_out, const LatticeArgs& a, cudaStream_t s) {
   const dim3 grid = site_grid(a), block(ABX, ABY);
   if (prec == LBM_FP64)
-    moments_vjp_kernel<LBM_FP64><<<grid, block, 0, s>>>(f, g_rho, g_ux, g_uy, g_T, lam_out, a);
+    moments_vjp_kernel<LBM_FP64, R><<<grid, block, 0, s>>>(f, g_rho, g_ux, g_uy, g_T, lam_out, a);
   else
-    moments_vjp_kernel<LBM_FP32_SHIFTED><<<grid, block, 0, s>>>(f, g_rho, g_ux, g_uy, g_T, lam_out, a);
+    moments_vjp_kernel<LBM_FP32_SHIFTED, R><<<grid, block, 0, s>>>(f, g_rho, g_ux, g_uy, g_T, lam_out, a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux, const double* g_uy,
+                               const double* g_T, double* lam_out, const LatticeArgs& a, cudaStream_t s) {
+  return launch_moments_vjp_t(prec, f, g_rho, g_ux, g_uy, g_T, lam_out, a, s);
+}
+
+cudaError_t launch_moments_vjp_f32(int prec, const void* f, const double* g_rho, const double* g_ux,
+                                   const double* g_uy, const double* g_T, float* lam_out, const LatticeArgs& a,
+                                   cudaStream_t s) {
+  return launch_moments_vjp_t(prec, f, g_rho, g_ux, g_uy, g_T, lam_out, a, s);
 }
 
 cudaError_t launch_init_vjp(const double* rho, const double* ux, const double* uy, const double* T,
                             const double* lam, double* g_rho, double* g_ux, double* g_uy, double* g_T,
                             const LatticeArgs& a, cudaStream_t s) {
+  init_vjp_kernel<<<site_grid(a), dim3(ABX, ABY), 0, s>>>(rho, ux, uy, T, lam, g_rho, g_ux, g_uy, g_T, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_vjp_f32(const double* rho, const double* ux, const double* uy, const double* T,
+                                const float* lam, double* g_rho, double* g_ux, double* g_uy, double* g_T,
+                                const LatticeArgs& a, cudaStream_t s) {
   init_vjp_kernel<<<site_grid(a), dim3(ABX, ABY), 0, s>>>(rho, ux, uy, T, lam, g_rho, g_ux, g_uy, g_T, a);
   return cudaGetLastError();
 }

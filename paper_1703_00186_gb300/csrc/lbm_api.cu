@@ -34,6 +34,14 @@ cudaError_t launch_adjoint(int prec, const void* f_t, const double* lam_in, doub
 cudaError_t launch_moments_vjp(int prec, const void* f, const double* g_rho, const double* g_ux,
                                const double* g_uy, const double* g_T, double* lam_out,
                                const LatticeArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_f32(const void* f_t, const float* lam_in, float* lam_out, const LatticeArgs& a,
+                               cudaStream_t s);
+cudaError_t launch_moments_vjp_f32(int prec, const void* f, const double* g_rho, const double* g_ux,
+                                   const double* g_uy, const double* g_T, float* lam_out, const LatticeArgs& a,
+                                   cudaStream_t s);
+cudaError_t launch_init_vjp_f32(const double* rho, const double* ux, const double* uy, const double* T,
+                                const float* lam, double* g_rho, double* g_ux, double* g_uy, double* g_T,
+                                const LatticeArgs& a, cudaStream_t s);
 cudaError_t launch_init_vjp(const double* rho, const double* ux, const double* uy, const double* T,
                             const double* lam, double* g_rho, double* g_ux, double* g_uy,
                             double* g_T, const LatticeArgs& a, cudaStream_t s);
@@ -502,6 +510,35 @@ int lbm_init_vjp(lbm_ctx* c, const double* rho, const double* ux, const double* 
   if (!rho || !ux || !uy || !T || !lam) return fail(c, LBM_ERR_INVALID, "lbm_init_vjp: NULL input");
   return cuda_check(c, launch_init_vjp(rho, ux, uy, T, lam, g_rho, g_ux, g_uy, g_T, c->args, c->stream),
                     "lbm_init_vjp");
+}
+
+int lbm_adjoint_step_f32(lbm_ctx* c, const void* f_t, const float* lam_in, float* lam_out) {
+  if (!c) return LBM_ERR_INVALID;
+  if (c->p.precision != LBM_FP32_SHIFTED)
+    return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step_f32: LBM_FP32_SHIFTED contexts only");
+  if (!f_t || !lam_in || !lam_out || (const void*)lam_in == (const void*)lam_out)
+    return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step_f32: bad buffers");
+  if (c->args.regularized)
+    return fail(c, LBM_ERR_INVALID, "lbm_adjoint_step_f32: no adjoint of the regularised collide");
+  return cuda_check(c, launch_adjoint_f32(f_t, lam_in, lam_out, c->args, c->stream), "lbm_adjoint_step_f32");
+}
+
+int lbm_moments_vjp_f32(lbm_ctx* c, const void* f, const double* g_rho, const double* g_ux, const double* g_uy,
+                        const double* g_T, float* lam_out) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!f || !lam_out) return fail(c, LBM_ERR_INVALID, "lbm_moments_vjp_f32: bad buffers");
+  return cuda_check(c,
+                    launch_moments_vjp_f32(storage_prec(c->p.precision), f, g_rho, g_ux, g_uy, g_T, lam_out, c->args,
+                                           c->stream),
+                    "lbm_moments_vjp_f32");
+}
+
+int lbm_init_vjp_f32(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T,
+                     const float* lam, double* g_rho, double* g_ux, double* g_uy, double* g_T) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!rho || !ux || !uy || !T || !lam) return fail(c, LBM_ERR_INVALID, "lbm_init_vjp_f32: NULL input");
+  return cuda_check(c, launch_init_vjp_f32(rho, ux, uy, T, lam, g_rho, g_ux, g_uy, g_T, c->args, c->stream),
+                    "lbm_init_vjp_f32");
 }
 
 int lbm_check_finite(lbm_ctx* c, const void* f, int* ok) {

@@ -130,14 +130,18 @@ class Lattice:
     def _opt_state(self, t, name):
         return None if t is None else self._state(t, name)
 
-    def _cotangent(self, t, name):
-        return _check_tensor(t, name, torch.float64, self.shape, self.device)
+    def _cotangent(self, t, name, dtype=torch.float64):
+        return _check_tensor(t, name, dtype, self.shape, self.device)
 
     def new_state(self, fill=float("nan")):
         return torch.full(self.shape, fill, dtype=self.dtype, device=self.device)
 
-    def new_cotangent(self, fill=float("nan")):
-        return torch.full((NPOP, self.ly + 2 * HALO, self.lx), fill, dtype=torch.float64, device=self.device)
+    def new_cotangent(self, fill=float("nan"), dtype=torch.float64):
+        """A cotangent buffer in the state layout: float64, or float32 for the
+        float32 adjoint of FP32-store lattices (adjoint_step dispatches on it)."""
+        if dtype not in (torch.float64, torch.float32):
+            raise ValueError(f"cotangent dtype {dtype}: float64 or float32")
+        return torch.full((NPOP, self.ly + 2 * HALO, self.lx), fill, dtype=dtype, device=self.device)
 
     # ------------------------------------------------------------------
     def init(self, rho, ux, uy, T):
@@ -249,29 +253,40 @@ class Lattice:
         return dst
 
     def adjoint_step(self, f_t: torch.Tensor, lam_in: torch.Tensor, lam_out: torch.Tensor | None = None):
+        """lam_out = P^T B^T C^T lam_in at state f_t; float32 cotangents take
+        the float32 adjoint (FP32-store lattices only)."""
         self._state(f_t, "f_t")
-        self._cotangent(lam_in, "lam_in")
+        if not isinstance(lam_in, torch.Tensor):
+            raise TypeError("lam_in: expected a torch tensor")
+        dt = lam_in.dtype
+        self._cotangent(lam_in, "lam_in", dt)
         if lam_out is None:
-            lam_out = self.new_cotangent()
-        self._cotangent(lam_out, "lam_out")
-        self._check(self.lib.lbm_adjoint_step(self.ctx, _ptr(f_t), _ptr(lam_in), _ptr(lam_out)))
+            lam_out = self.new_cotangent(dtype=dt)
+        self._cotangent(lam_out, "lam_out", dt)
+        fn = self.lib.lbm_adjoint_step_f32 if dt == torch.float32 else self.lib.lbm_adjoint_step
+        self._check(fn(self.ctx, _ptr(f_t), _ptr(lam_in), _ptr(lam_out)))
         return lam_out
 
-    def moments_vjp(self, f, g_rho=None, g_ux=None, g_uy=None, g_T=None, lam_out=None):
+    def moments_vjp(self, f, g_rho=None, g_ux=None, g_uy=None, g_T=None, lam_out=None, dtype=torch.float64):
         self._state(f, "f")
         if lam_out is None:
-            lam_out = self.new_cotangent()
-        self._cotangent(lam_out, "lam_out")
+            lam_out = self.new_cotangent(dtype=dtype)
+        dt = lam_out.dtype if isinstance(lam_out, torch.Tensor) else dtype
+        self._cotangent(lam_out, "lam_out", dt)
         gs = [None if g is None else _field(g, self.ly, self.lx, self.device) for g in (g_rho, g_ux, g_uy, g_T)]
-        self._check(self.lib.lbm_moments_vjp(self.ctx, _ptr(f), *[_ptr(g) for g in gs], _ptr(lam_out)))
+        fn = self.lib.lbm_moments_vjp_f32 if dt == torch.float32 else self.lib.lbm_moments_vjp
+        self._check(fn(self.ctx, _ptr(f), *[_ptr(g) for g in gs], _ptr(lam_out)))
         self._keep = gs
         return lam_out
 
     def init_vjp(self, rho, ux, uy, T, lam):
         f = [_field(v, self.ly, self.lx, self.device) for v in (rho, ux, uy, T)]
-        self._cotangent(lam, "lam")
+        if not isinstance(lam, torch.Tensor):
+            raise TypeError("lam: expected a torch tensor")
+        self._cotangent(lam, "lam", lam.dtype if lam.dtype == torch.float32 else torch.float64)
         out = [torch.empty((self.ly, self.lx), dtype=torch.float64, device=self.device) for _ in range(4)]
-        self._check(self.lib.lbm_init_vjp(self.ctx, *[_ptr(t) for t in f], _ptr(lam), *[_ptr(t) for t in out]))
+        fn = self.lib.lbm_init_vjp_f32 if lam.dtype == torch.float32 else self.lib.lbm_init_vjp
+        self._check(fn(self.ctx, *[_ptr(t) for t in f], _ptr(lam), *[_ptr(t) for t in out]))
         self._keep = f
         return tuple(out)
 

@@ -141,3 +141,58 @@ def test_moments_vjp_fp32_state_parity():
     lat = make(p, precision="fp32", rho0=rho0)
     got = lat.moments_vjp(to_dev(d, torch.float32), *g).cpu().numpy()
     assert plane_err(got, want) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Float32 cotangents (lbm_adjoint_step_f32, FP32-store lattices).  Every
+# cotangent sum and the relaxation run in float32: each result carries a few
+# float32 roundings (unit 6e-8) of terms up to about 10 times the plane's
+# largest value, so the bar is 2e-6 of the plane's max |oracle| (measured
+# 2-4e-7).  The oracle takes the float32 cotangents exactly (as float64).
+
+@pytest.mark.parametrize("lx,ly,periodic_y", [(16, 12, False), (35, 7, True), (40, 24, False)])
+def test_adjoint_step_f32_parity(lx, ly, periodic_y):
+    rho0 = 1.05
+    p = M.Params(lx, ly, tau=0.75, g=1e-3, t_top=0.9, t_bottom=1.1, periodic_y=periodic_y)
+    f = noisy_state(lx, ly, 70 + lx)
+    d = (f - K["w"][:, None, None] * rho0).astype(np.float32)
+    fdec = d.astype(np.float64) + K["w"][:, None, None] * rho0
+    lam32 = rand_cot(lx, ly, 71 + ly).astype(np.float32)
+    want = A.adjoint_step(fdec, lam32.astype(np.float64), p)
+    lat = make(p, precision="fp32", rho0=rho0)
+    got = lat.adjoint_step(to_dev(d, torch.float32), to_dev(lam32, torch.float32))
+    assert got.dtype == torch.float32
+    assert plane_err(got.cpu().numpy().astype(np.float64), want) <= 2e-6
+
+
+def test_adjoint_step_f32_is_for_fp32_store_lattices_only():
+    from paper_1703_00186_gb300._lib import LBMError
+    p = M.Params(16, 12, tau=0.8)
+    lat = make(p)
+    f = to_dev(noisy_state(16, 12, 80))
+    lam = to_dev(rand_cot(16, 12, 81), torch.float32)
+    with pytest.raises(LBMError):
+        lat.adjoint_step(f, lam)
+
+
+def test_moments_and_init_vjp_with_float32_cotangents():
+    # computed in float64 and rounded once (moments), or read from float32
+    # (init): the float32 rounding of the cotangents is the only difference
+    lx, ly = 21, 9
+    rho0 = 1.05
+    p = M.Params(lx, ly, tau=0.8)
+    f = noisy_state(lx, ly, 90)
+    d = (f - K["w"][:, None, None] * rho0).astype(np.float32)
+    fdec = d.astype(np.float64) + K["w"][:, None, None] * rho0
+    g = [np.random.default_rng(91 + i).standard_normal((ly, lx)) for i in range(4)]
+    lat = make(p, precision="fp32", rho0=rho0)
+    got = lat.moments_vjp(to_dev(d, torch.float32), *g, dtype=torch.float32)
+    assert got.dtype == torch.float32
+    want = A.moments_vjp(fdec, *g)
+    assert plane_err(got.cpu().numpy().astype(np.float64), want) <= 1e-7
+    rho, ux, uy, T = synth.random_fields(lx, ly, 92, umax=0.1)
+    lam32 = rand_cot(lx, ly, 93).astype(np.float32)
+    gq = [t.cpu().numpy() for t in lat.init_vjp(rho, ux, uy, T, to_dev(lam32, torch.float32))]
+    wq = A.equilibrium_vjp(rho, ux, uy, T, lam32.astype(np.float64))
+    for a, b in zip(gq, wq):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
