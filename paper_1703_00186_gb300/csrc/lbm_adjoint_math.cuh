@@ -66,31 +66,6 @@ __device__ __forceinline__ EqCot eq_cotangent(GetLam lam, double v_x, double v_y
 
 namespace lbm {
 
-// Coefficients of Q(xi) = a(c2) + b(c2) cu + c(c2) cu^2 + d cu^3 + e cu^4 in the
-// integer-velocity monomials of degree <= 4 (order N00 N20 N02 N40 N22 N04
-// N10 N30 N12 N01 N03 N21 N11 N31 N13), with cu = vx xi_x + vy xi_y,
-// c2 = r2 |xi|^2, a = a0 + a1 c2 + a2 c2^2, b = b0 + b1 c2, c = c0 + c1 c2.
-__device__ __forceinline__ void poly_monomials(double a0, double a1, double a2, double b0, double b1, double c0,
-                                               double c1, double d, double e, double vx, double vy, double r2,
-                                               double (&Q)[15]) {
-  const double vx2 = vx * vx, vy2 = vy * vy, vxy = vx * vy, r4 = r2 * r2;
-  Q[0] = a0;
-  Q[1] = fma(a1, r2, c0 * vx2);
-  Q[2] = fma(a1, r2, c0 * vy2);
-  Q[3] = fma(a2, r4, fma(c1 * r2, vx2, e * vx2 * vx2));
-  Q[4] = fma(2.0 * a2, r4, fma(c1 * r2, vx2 + vy2, 6.0 * e * vx2 * vy2));
-  Q[5] = fma(a2, r4, fma(c1 * r2, vy2, e * vy2 * vy2));
-  Q[6] = b0 * vx;
-  Q[7] = vx * fma(b1, r2, d * vx2);
-  Q[8] = vx * fma(b1, r2, 3.0 * d * vy2);
-  Q[9] = b0 * vy;
-  Q[10] = vy * fma(b1, r2, d * vy2);
-  Q[11] = vy * fma(b1, r2, 3.0 * d * vx2);
-  Q[12] = 2.0 * c0 * vxy;
-  Q[13] = vxy * fma(2.0 * c1, r2, 4.0 * e * vx2);
-  Q[14] = vxy * fma(2.0 * c1, r2, 4.0 * e * vy2);
-}
-
 // The 15 w-weighted cotangent moments Lam_(c,e) = sum_l w_l lam_l xi_lx^c
 // xi_ly^e (order N00 N20 N02 N40 N22 N04 N10 N30 N12 N01 N03 N21 N11 N31 N13)
 // from group sums: the 18 +- pairs fall into the x-axis pairs (a, 0), the
@@ -202,9 +177,9 @@ __device__ __forceinline__ EqCot eq_cotangent_mono(const double (&L)[15], double
   const double vx2 = v_x * v_x, vy2 = v_y * v_y, vxy = v_x * v_y;
   const double B01r2 = B.B01 * r2, B02r4 = B.B02 * r4, B21r2 = B.B21 * r2, B11r2 = B.B11 * r2;
   const double vx2_6 = vx2 * (1.0 / 6.0), vy2_6 = vy2 * (1.0 / 6.0);
-  // The monomial coefficients of the four polynomials (poly_monomials with
-  // the coefficients of P, dP/dU2, dP/dtheta and P_cu), written out so that
-  // their zero coefficients cost nothing.
+  // The monomial coefficients of the four polynomials (P, dP/dU2, dP/dtheta
+  // and P_cu expanded from cu = xi . v and c2 = r^2 |xi|^2), written out so
+  // that their zero coefficients cost nothing.
   EqCot s;
   {  // P = A0 + A1 cu + A2 cu^2 + cu^3 / 6 + cu^4 / 24
     const double P1 = fma(B.B20, vx2, B01r2), P2 = fma(B.B20, vy2, B01r2);
