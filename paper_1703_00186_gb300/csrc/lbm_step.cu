@@ -162,8 +162,10 @@ __global__ void __launch_bounds__(BX * BY, 4) step_observe_kernel(const double* 
         q[i] = fix_add(q[i], other);
       }
     }
+    if ((threadIdx.x & 31) == 0) {  // only the lane that adds to the totals rounds
 #pragma unroll
-    for (int i = 0; i < NOBS; ++i) o[i] = fix_to_double(q[i]);
+      for (int i = 0; i < NOBS; ++i) o[i] = fix_to_double(q[i]);
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < NOBS; ++i) {
