@@ -42,12 +42,12 @@ struct Codec<LBM_FP32_SHIFTED> {
   __device__ float enc(int l, double v) const { return (float)(v - a->w_rho0[l]); }
 };
 
-// The regularised collide is latency-bound on its fixed-point sums: capping
-// it at 96 registers (5 blocks per SM, some spills) measured 27% faster than
-// the unconstrained 163 registers (3 blocks).  The double-float collide gains
-// 2-3% from the same cap (60 bytes of spill, 4 -> 5 blocks per SM).
+// Occupancy caps, as measured: the double-float step with its pair groups
+// unrolled runs best at 128 registers (4 blocks per SM, no spills; a
+// 96-register cap spills and is 1.5 % slower), the regularised step at 128
+// (4 blocks; 96 spills, 163 unconstrained is slower).
 #ifndef LBM_DF_MINB
-#define LBM_DF_MINB 5  // minimum resident blocks per SM of the double-float step
+#define LBM_DF_MINB 4  // minimum resident blocks per SM of the double-float step
 #endif
 #ifndef LBM_FP64_FIX
 #define LBM_FP64_FIX 1  // float64 BGK step: equilibrium polynomial on the integer pipe
