@@ -629,6 +629,10 @@ __host__ __device__ constexpr int shell_first_pair(int j) {
   return j == 1 ? 0 : j == 2 ? 2 : j == 3 ? 4 : j == 4 ? 6 : j == 5 ? 10 : j == 6 ? 12 : j == 7 ? 14 : 18;
 }
 
+#ifndef LBM_DF_GROUP_UNROLL
+#define LBM_DF_GROUP_UNROLL 2  // unrolling of the double-float collide's loop over a shell's pair groups
+#endif
+constexpr int kDfGroupUnroll = LBM_DF_GROUP_UNROLL;
 
 // BGK collide on float64 populations, balancing the FP64 and FP32 pipes
 // (GB300 issues FP64 at 1/64 of the FP32 rate).  The moment sums, 1/rho, u and
@@ -636,10 +640,9 @@ __host__ __device__ constexpr int shell_first_pair(int j) {
 // coefficients and the per-population equilibrium polynomial run in
 // double-float (about 48 significant bits) on the FP32 pipe; the relaxation is
 // one float64 FMA, f <- (1 - omega) f + f^eq, with f^eq recombined from its two
-// words by one float64 add.  The populations wait in shared memory for the
-// relaxation; the loops over shells and pair groups are unrolled (measured
-// faster than rolled, at 4 blocks per SM).  The results are written to dst
-// directly.
+// words by one float64 add.  The pair loop is rolled (the populations are read
+// back from shared memory) to keep the instruction footprint small.  The
+// results are written to dst directly.
 template <int NT>
 __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const LatticeArgs& a, double (*s_f)[NT],
                                                 int tid, double* __restrict__ dst, int x, int y) {
@@ -683,7 +686,7 @@ __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const Lattice
     const float2 nsc = f2s(-sc.hi);
     // two pairs of the shell per iteration, one in each lane (every shell
     // holds an even number of pairs)
-#pragma unroll
+#pragma unroll kDfGroupUnroll
     for (int g = shell_first_pair(j) / 2; g < shell_first_pair(j + 1) / 2; ++g) {
       const float2 rx = f2(c_pair_rep_x2[g][0], c_pair_rep_x2[g][1]);
       const float2 nrx = f2(c_pair_rep_x2[g][2], c_pair_rep_x2[g][3]);
