@@ -640,9 +640,10 @@ constexpr int kDfGroupUnroll = LBM_DF_GROUP_UNROLL;
 // coefficients and the per-population equilibrium polynomial run in
 // double-float (about 48 significant bits) on the FP32 pipe; the relaxation is
 // one float64 FMA, f <- (1 - omega) f + f^eq, with f^eq recombined from its two
-// words by one float64 add.  The pair loop is rolled (the populations are read
-// back from shared memory) to keep the instruction footprint small.  The
-// results are written to dst directly.
+// words by one float64 add.  The populations wait in shared memory for the
+// relaxation.  The loop over a shell's pair groups (one or two) carries an
+// unroll count of two: 4075 MLUPS against 3890 rolled and 3493 with a plain
+// full-unroll pragma, as measured.  The results are written to dst directly.
 template <int NT>
 __device__ __forceinline__ void collide_fp64_df(double (&f)[NPOP], const LatticeArgs& a, double (*s_f)[NT],
                                                 int tid, double* __restrict__ dst, int x, int y) {
