@@ -156,7 +156,7 @@ def test_bounded_barrier_wait_times_out_and_batch_stays_usable():
         assert plane_err(b.state(i).cpu().numpy(), oracle_run(s, flds[i], 3)) <= 1e-12
 
 
-@pytest.mark.parametrize("tile", [0, 8, 9])
+@pytest.mark.parametrize("tile", [0, 1, 5, 8, 9])
 def test_batch_fp64df_matches_oracle(tile):
     # float64 storage with the double-float collide, graph and persistent launches
     specs, flds = build("fp64df")
