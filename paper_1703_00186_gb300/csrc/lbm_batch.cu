@@ -116,7 +116,7 @@ __device__ __forceinline__ void batch_tile(const BatchEntry* __restrict__ ent, c
       __shared__ double s_f[NPOP][TBX * TBY];
       collide_fp64_df<TBX * TBY>(f, a, s_f, tid, dst, x, y);
     } else if constexpr (PREC == LBM_FP64 && TBX * TBY <= 128) {
-      __shared__ double s_f[NPOP][TBX * TBY];  // within the 48 KB of static shared memory
+      __shared__ double s_f[NPOP][TBX * TBY];  // 37.9 KB per 128-thread tile; larger tiles keep collide_fp64
       collide_fp64_fix<TBX * TBY>(f, a, s_f, tid, dst, x, y);
     } else {
       if constexpr (PREC == LBM_FP64)
