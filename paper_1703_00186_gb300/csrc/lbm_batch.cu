@@ -402,14 +402,30 @@ cudaError_t launch_tile_i(long long blocks, const BatchEntry* ent, const long lo
   return cudaGetLastError();
 }
 
+// The wall rows (batch_edge_kernel) run on the side stream `aux`, forked
+// from and joined back to `s` around the interior launch: the two write
+// disjoint sites of the same step and may overlap.
 cudaError_t launch_param_tile(int i, const ParamTable& t, long long blocks, long long edges, const LatticeArgs& m,
-                              int parity, cudaStream_t s) {
+                              int parity, cudaStream_t s, cudaStream_t aux, cudaEvent_t ev_fork,
+                              cudaEvent_t ev_join) {
   if (edges > 0) {
-    batch_edge_kernel<<<(unsigned)((edges + 127) / 128), 128, 0, s>>>(t, m, parity, edges);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaEventRecord(ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_fork, 0);
     if (e != cudaSuccess) return e;
+    batch_edge_kernel<<<(unsigned)((edges + 127) / 128), 128, 0, aux>>>(t, m, parity, edges);
+    e = cudaGetLastError();
+    const cudaError_t r = cudaEventRecord(ev_join, aux);  // joined back below, also after an error
+    if (e != cudaSuccess) {
+      cudaStreamWaitEvent(s, ev_join, 0);
+      return e;
+    }
+    if (r != cudaSuccess) return r;
   }
-  if (blocks <= 0) return cudaSuccess;
+  const auto join = [&](cudaError_t e) {
+    const cudaError_t w = edges > 0 ? cudaStreamWaitEvent(s, ev_join, 0) : cudaSuccess;
+    return e != cudaSuccess ? e : w;
+  };
+  if (blocks <= 0) return join(cudaSuccess);
   const dim3 grid((unsigned)blocks), block(32, 4);
   if (kParamRows[i] == 1)
     batch_param_kernel<32, 4, 1><<<grid, block, 0, s>>>(t, m, parity);
@@ -417,7 +433,7 @@ cudaError_t launch_param_tile(int i, const ParamTable& t, long long blocks, long
     batch_param_kernel<32, 4, 4><<<grid, block, 0, s>>>(t, m, parity);
   else
     batch_param_kernel<32, 4, 8><<<grid, block, 0, s>>>(t, m, parity);
-  return cudaGetLastError();
+  return join(cudaGetLastError());
 }
 
 template <int PREC>
@@ -457,6 +473,7 @@ struct lbm_batch {
   long long sites;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (n, parity, tile)
   cudaStream_t aux[kAux];  // per-lattice launches: the lattices' streams
+  cudaEvent_t ev_fork, ev_join;  // the wall-row launch of the parameter-table candidates
   std::vector<int> order;  // lattices by decreasing size
   std::vector<int> lane;   // stream of each lattice (balanced by sites)
   GridBarrier* d_bar;  // persistent-kernel barrier state
@@ -497,7 +514,8 @@ cudaError_t launch_batch(const lbm_batch* b, int parity, cudaStream_t s) {
     if (b->param_ok) {
       for (size_t g = 0; g < b->ptab[i].size(); ++g) {
         const cudaError_t e =
-            launch_param_tile(i, b->ptab[i][g], b->pblocks[i][g], b->pedges[i][g], b->args[0], parity, s);
+            launch_param_tile(i, b->ptab[i][g], b->pblocks[i][g], b->pedges[i][g], b->args[0], parity, s,
+                              b->aux[0], b->ev_fork, b->ev_join);
         if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
@@ -523,6 +541,8 @@ void free_batch(lbm_batch* b) {
   if (b->capture) cudaStreamDestroy(b->capture);
   for (int k = 0; k < kAux; ++k)
     if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
 }
 
@@ -754,6 +774,12 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_lattice_desc* descs, int 
       free_batch(b);
       return LBM_ERR_CUDA;
     }
+  }
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return LBM_ERR_CUDA;
   }
   // per-lattice launches: largest lattices first, each to the stream with the
   // fewest sites so far
