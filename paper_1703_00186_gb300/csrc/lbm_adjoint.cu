@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(ABX * ABY, LBM_ADJ_MINB) adjoint_kernel(const 
   const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
   const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * v_x, s.SU, s.Scx));
   const double gJy = a.r2 * fma(-s.Sth, sf.uy, fma(2.0 * a.inv_r2 * v_y, s.SU, s.Scy));
-  const double gE = 0.5 * a.r2 * s.Sth;
+  const double gE = a.r2_2 * s.Sth;
   const double gR = s.SP - a.r2 * (sf.ux * (s.Scx + 2.0 * a.inv_r2 * v_x * s.SU) +
                                    sf.uy * (s.Scy + 2.0 * a.inv_r2 * v_y * s.SU)) +
-                    s.Sth * fma(0.5 * a.r2, usq, -sf.T);
+                    s.Sth * fma(a.r2_2, usq, -sf.T);
   const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
   // mu_l = (1 - omega) lam_l + omega (gR + gJ . xi_l + gE |xi_l|^2)
   double mu[NPOP];
@@ -258,10 +258,10 @@ __global__ void __launch_bounds__(ABX * ABY) adjoint_df_kernel(const void* __res
   const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
   const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * vxd, s.SU, s.Scx));
   const double gJy = a.r2 * fma(-s.Sth, sf.uy, fma(2.0 * a.inv_r2 * vyd, s.SU, s.Scy));
-  const double gE = 0.5 * a.r2 * s.Sth;
+  const double gE = a.r2_2 * s.Sth;
   const double gR = s.SP - a.r2 * (sf.ux * (s.Scx + 2.0 * a.inv_r2 * vxd * s.SU) +
                                    sf.uy * (s.Scy + 2.0 * a.inv_r2 * vyd * s.SU)) +
-                    s.Sth * fma(0.5 * a.r2, usq, -sf.T);
+                    s.Sth * fma(a.r2_2, usq, -sf.T);
   const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
   // mu_l = (1 - omega) lam_l + omega (gR + gJ . xi_l + gE |xi_l|^2), pushed
   // back to its pull source as it is formed (P^T; wall slots reduce), in a
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(ABX * ABY) moments_vjp_kernel(const void* __re
   const double gy = g_uy ? g_uy[i] : 0.0;
   const double gt = g_T ? g_T[i] : 0.0;
   const double ku = a.r * sf.inv;                 // d u / d f = r (xi - u_xi) / rho
-  const double kt = 0.5 * a.r2 * sf.inv * gt;     // (r^2 / (2 rho)) g_T
+  const double kt = a.r2_2 * sf.inv * gt;     // (r^2 / (2 rho)) g_T
   const double base = gr - gt * sf.T * sf.inv;
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) {

@@ -213,6 +213,9 @@ __device__ __forceinline__ void param_tile(const ParamTable& t, const LatticeArg
   const long long tl = b - e.tile_start;
   const int ty = (int)(tl / e.tiles_x), tx = (int)(tl - (long long)ty * e.tiles_x);
   const int x = tx * TBX + threadIdx.x;
+  // a tile holding a seam column takes the wrapped offsets for all its lanes
+  // (block-uniform, so no warp runs both paths)
+  const bool seam_tile = LBM_SEAM_UNIFORM ? (tx * TBX < 3 || tx * TBX + TBX > lx - 3) : (x < 3 || x >= lx - 3);
   const float* __restrict__ src = static_cast<const float*>(e.f[parity]);
   float* __restrict__ dst = static_cast<float*>(const_cast<void*>(e.f[parity ^ 1]));
 #pragma unroll 1
@@ -222,7 +225,7 @@ __device__ __forceinline__ void param_tile(const ParamTable& t, const LatticeArg
       float f[NPOP];
       const int site = (y + HALO) * lx + x;
       if (y < 3 || y >= ly - 3) continue;  // wall rows: batch_edge_kernel
-      if (x >= 3 && x < lx - 3) {
+      if (!seam_tile) {
         const char* s = reinterpret_cast<const char*>(src + site);
 #pragma unroll
         for (int l = 0; l < NPOP; ++l) f[l] = load<COHERENT>(reinterpret_cast<const float*>(s + e.pull_off[l]));

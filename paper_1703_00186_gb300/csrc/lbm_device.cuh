@@ -56,6 +56,19 @@ __device__ __forceinline__ bool fast_site(const LatticeArgs& a, int x) {
   return a.idx32 && !a.periodic_y && x >= 3 && x < a.lx - 3;
 }
 
+#ifndef LBM_SEAM_UNIFORM
+#define LBM_SEAM_UNIFORM 1
+#endif
+// fast_site for every lane of the warp holding column x (a warp is a row
+// segment of 32 columns starting at x - lane): a warp that reaches a seam
+// column takes the general pull for all its lanes instead of running both
+// paths one after the other.
+__device__ __forceinline__ bool fast_warp(const LatticeArgs& a, int x) {
+  if (!LBM_SEAM_UNIFORM) return fast_site(a, x);
+  const int x0 = x - (int)(threadIdx.x & 31u);
+  return a.idx32 && !a.periodic_y && x0 >= 3 && x0 + 32 <= a.lx - 3;
+}
+
 // pull at a fast site: one address computation per population.
 template <typename T, bool COHERENT = false>
 __device__ __forceinline__ void pull_fast(const T* __restrict__ src, int site, const LatticeArgs& a,
@@ -367,7 +380,7 @@ __device__ __forceinline__ SiteFields site_fields(const Moments& m, const Lattic
   s.inv = 1.0 / m.rho;
   s.ux = m.Jx * s.inv;
   s.uy = m.Jy * s.inv;
-  s.T = 0.5 * a.r2 * fma(m.Exi, s.inv, -fma(s.ux, s.ux, s.uy * s.uy));
+  s.T = a.r2_2 * fma(m.Exi, s.inv, -fma(s.ux, s.ux, s.uy * s.uy));
   return s;
 }
 
@@ -749,24 +762,26 @@ __device__ __forceinline__ void eq_monomials(const SiteFields& sf, const Lattice
   const double theta = sf.T + a.tshift;
   const double uys = sf.uy - a.tau_g_xi;
   const double vx_ = a.r2 * sf.ux, vy_ = a.r2 * uys;
-  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
+  const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
+  const double v2 = vx2 + vy2;
+  const double U2 = v2 * a.inv_r2;  // |u|^2 r^2
   // the Hermite coefficients of eq_coef that enter without a theta multiple
   // (B11 r^2 = theta r^2 / 2, B21 r^2 = theta r^2 / 4 and B02 r^4 = theta^2
   // r^4 / 8 use the lattice's multiples of r^2 and r^4)
-  const double h = fma(-0.25, U2, 0.5);
+  const double h = fma(-0.25, U2, 0.5), h2 = fma(-0.5, U2, 1.0);  // h2 = 2 h exactly
   const double B20 = fma(-1.5, theta, h);
-  const double B10 = fma(-2.0, theta, fma(-0.5, U2, 1.0));
-  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(U2, fma(0.125, U2, -0.5), 1.0));
-  const double B01r2 = (theta * a.r2) * (h - theta);
+  const double B10 = fma(-2.0, theta, h2);  // = 2 (h - theta), rounded once
+  // 1 - U2 / 2 + U2^2 / 8 = 2 h^2 + 1/2
+  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(h2, h, 0.5));
   const double th2 = theta * theta;
   const double t4 = theta * a.r2_4, t2 = theta * a.r2_2;
-  const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
+  const double B01r2 = t2 * B10;  // theta r^2 (h - theta)
   const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);  // B11 r^2 + v^2 / 6
   P[0] = B00;
   P[1] = fma(B20, vx2, B01r2);
   P[2] = fma(B20, vy2, B01r2);
   P[3] = fma(th2, a.r4_8, vx2 * fma(vx2, 1.0 / 24.0, t4));
-  P[4] = fma(th2, a.r4_4, fma(t4, vx2 + vy2, 0.25 * (vx2 * vy2)));
+  P[4] = fma(th2, a.r4_4, fma(t4, v2, 0.25 * (vx2 * vy2)));
   P[5] = fma(th2, a.r4_8, vy2 * fma(vy2, 1.0 / 24.0, t4));
   P[6] = B10 * vx_;
   P[7] = vx_ * I;

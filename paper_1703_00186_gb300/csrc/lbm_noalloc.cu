@@ -89,10 +89,10 @@ __global__ void __launch_bounds__(128) noalloc_adjoint_kernel(const void* __rest
   const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
   const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * v_x, s.SU, s.Scx));
   const double gJy = a.r2 * fma(-s.Sth, sf.uy, fma(2.0 * a.inv_r2 * v_y, s.SU, s.Scy));
-  const double gE = 0.5 * a.r2 * s.Sth;
+  const double gE = a.r2_2 * s.Sth;
   const double gR = s.SP - a.r2 * (sf.ux * (s.Scx + 2.0 * a.inv_r2 * v_x * s.SU) +
                                    sf.uy * (s.Scy + 2.0 * a.inv_r2 * v_y * s.SU)) +
-                    s.Sth * fma(0.5 * a.r2, usq, -sf.T);
+                    s.Sth * fma(a.r2_2, usq, -sf.T);
   const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
   double mu[NPOP];
   mu[0] = fma(a.omc, lam[0], wR);

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(BX * BY, REG ? LBM_REG_MINB : DFARITH ? LBM_DF
   T* __restrict__ dst = static_cast<T*>(dst_);
   Codec<PREC> codec{&a};
   T f[NPOP];
-  if (fast_site(a, x)) pull_fast(src, site_off(a, y, x), a, f);
+  if (fast_warp(a, x)) pull_fast(src, site_off(a, y, x), a, f);
   else pull(src, x, y, a, f);
   if constexpr (PREC == LBM_FP32_SHIFTED && F32M == FP32_ARITH_F64_COLLIDE) {
     if (COLLIDE) {
