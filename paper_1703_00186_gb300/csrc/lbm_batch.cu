@@ -215,7 +215,7 @@ __device__ __forceinline__ void param_tile(const ParamTable& t, const LatticeArg
   const int x = tx * TBX + threadIdx.x;
   // a tile holding a seam column takes the wrapped offsets for all its lanes
   // (block-uniform, so no warp runs both paths)
-  const bool seam_tile = LBM_SEAM_UNIFORM ? (tx * TBX < 3 || tx * TBX + TBX > lx - 3) : (x < 3 || x >= lx - 3);
+  const bool seam_tile = tx * TBX < 3 || tx * TBX + TBX > lx - 3;
   const float* __restrict__ src = static_cast<const float*>(e.f[parity]);
   float* __restrict__ dst = static_cast<float*>(const_cast<void*>(e.f[parity ^ 1]));
 #pragma unroll 1
