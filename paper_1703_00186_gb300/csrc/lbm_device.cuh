@@ -198,9 +198,11 @@ __device__ __forceinline__ Moments moment_sums(Get get) {
 // The same four sums formed exactly in 96-bit fixed point on the integer
 // pipe and rounded once to float64 (fixed96.cuh): the correctly rounded exact
 // sums.  Returns false, leaving `mo` unset, when a population lies outside
-// the fixed-point range (|f| >= 4, infinities, NaN).
-template <typename Get>
+// the fixed-point range (|f| >= 4, infinities, NaN).  EXI_D = -1 returns
+// E / 2 in place of E (an exact scaling of the same rounding).
+template <int EXI_D = 0, typename Get>
 __device__ __forceinline__ bool moment_sums_exact(Get get, Moments& mo) {
+  static_assert(EXI_D == 0 || EXI_D == -1, "E or E / 2");
   bool ok = true;
   Fix96 r = to_fix(get(0), ok);
   Fix96 jx{0u, 0u, 0u}, jy{0u, 0u, 0u}, e{0u, 0u, 0u};
@@ -217,7 +219,7 @@ __device__ __forceinline__ bool moment_sums_exact(Get get, Moments& mo) {
   mo.rho = fix_to_double(r);
   mo.Jx = fix_to_double(jx);
   mo.Jy = fix_to_double(jy);
-  mo.Exi = fix_to_double(e);
+  mo.Exi = fix_to_double_scaled(e, EXI_D);
   return true;
 }
 
@@ -225,11 +227,11 @@ __device__ __forceinline__ bool moment_sums_exact(Get get, Moments& mo) {
 // populations fit the fixed-point range, float64 additions (moment_sums) for
 // finite populations beyond it, and NaN moments for a site holding an
 // infinity or a NaN (so a diverged state stays non-finite, at the cost of
-// the normal path).
-template <typename Get>
+// the normal path).  EXI_D = -1: E / 2 in place of E.
+template <int EXI_D = 0, typename Get>
 __device__ __forceinline__ Moments site_moments(Get get) {
   Moments mo;
-  if (!moment_sums_exact(get, mo)) {
+  if (!moment_sums_exact<EXI_D>(get, mo)) {
     bool nonfinite = false;
 #pragma unroll
     for (int l = 0; l < NPOP; ++l)
@@ -239,6 +241,7 @@ __device__ __forceinline__ Moments site_moments(Get get) {
       mo = Moments{q, q, q, q};
     } else {
       mo = moment_sums(get);
+      if (EXI_D == -1) mo.Exi *= 0.5;
     }
   }
   return mo;
@@ -791,6 +794,68 @@ __device__ __forceinline__ void eq_monomials(const SiteFields& sf, const Lattice
   P[14] = vxy * J;
 }
 
+// 1 / x by one third-order Newton-Raphson correction of a float32 seed
+// (float64 FP-pipe work: three FMAs).  The seed y0 comes from x's top 23
+// significand bits (integer operations), the approximate float32 reciprocal
+// and an exact widening of its bits; with e = 1 - x y0 (|e| < 2^-21) the
+// correction y0 (1 + e + e^2) = (1 - e^3) / x leaves a relative error below
+// 2^-62 before the last rounding.  x outside [2^-125, 2^126) (zero,
+// subnormals, infinities, NaN included) gives NaN.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
+  const unsigned xf = (hi & 0x80000000u) | ((unsigned)(ex + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(xf)));
+  const unsigned rb = __float_as_uint(rf);
+  const unsigned yhi = (rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + (1023u - 127u)) << 20) | ((rb & 0x7fffffu) >> 3);
+  const double y0 = __hiloint2double((int)yhi, (int)(rb << 29));
+  const double e = fma(-x, y0, 1.0);
+  const double y = fma(y0, fma(e, e, e), y0);
+  return (ex >= -125 && ex < 126) ? y : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// eq_monomials for the float64 BGK step, straight from the moment sums
+// (rho, J and E / 2) with the site fields folded in, and with P[12] halved
+// (poly_to_fix<true> doubles it).  With s = r^2 / rho the shifted velocity is
+// v = (J_x s, J_y s - r^2 tau g / r) = r^2 (u - (0, tau g / r)), and
+//   theta = T + tshift,  T = (r^2 / 2) (E / rho - |u|^2),
+//   (r^2 / 2) |u|^2 = U2 / 2 + (tau g / r) v_y + (r^2 / 2) (tau g / r)^2,
+// so theta = (E / 2) s - U2 / 2 - (tau g / r) v_y + tshift_v, where the
+// lattice constant tshift_v = tshift - (r^2 / 2) (tau g / r)^2.  Products
+// of the theta multiples: theta^2 r^4 / 8 = t2 t4 and theta^2 r^4 / 4 = t2^2.
+__device__ __forceinline__ void eq_monomials_moments(const Moments& mh, const LatticeArgs& a, double (&P)[15]) {
+  const double s = a.r2 * rcp_nr(mh.rho);
+  const double vx_ = mh.Jx * s, vy_ = fma(mh.Jy, s, -a.r2_tau_g_xi);
+  const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
+  const double v2 = vx2 + vy2;
+  const double U2 = v2 * a.inv_r2;
+  const double theta = fma(mh.Exi, s, fma(-0.5, U2, fma(-a.tau_g_xi, vy_, a.tshift_v)));
+  const double h = fma(-0.25, U2, 0.5), h2 = fma(-0.5, U2, 1.0);  // h2 = 2 h exactly
+  const double B20 = fma(-1.5, theta, h);
+  const double B10 = fma(-2.0, theta, h2);  // = 2 (h - theta), rounded once
+  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(h2, h, 0.5));
+  const double t4 = theta * a.r2_4, t2 = theta * a.r2_2;
+  const double B01r2 = t2 * B10;
+  const double q8 = t2 * t4, q4 = t2 * t2;
+  const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);
+  P[0] = B00;
+  P[1] = fma(B20, vx2, B01r2);
+  P[2] = fma(B20, vy2, B01r2);
+  P[3] = fma(vx2, fma(vx2, 1.0 / 24.0, t4), q8);
+  P[4] = fma(t4, v2, fma(0.25 * vxy, vxy, q4));
+  P[5] = fma(vy2, fma(vy2, 1.0 / 24.0, t4), q8);
+  P[6] = B10 * vx_;
+  P[7] = vx_ * I;
+  P[8] = vx_ * fma(0.5, vy2, t2);
+  P[9] = B10 * vy_;
+  P[10] = vy_ * J;
+  P[11] = vy_ * fma(0.5, vx2, t2);
+  P[12] = B20 * vxy;  // half
+  P[13] = vxy * I;
+  P[14] = vxy * J;
+}
+
 // The regularised collide's coefficients R of the new populations
 // f_l = w_l R(xi_l) from the monomial moments N (same order as N).
 __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const LatticeArgs& a, double (&Rv)[15]) {
@@ -996,7 +1061,9 @@ __device__ __forceinline__ void grouped_moments(const FX& fx, Fix96 (&n)[15]) {
 // most 3^n in magnitude at the 37 velocities, so with |X| below 2^10, 2^8,
 // 2^6, 2^4 and 2^2 for degrees 0 to 4 every value of the polynomial, and so
 // every sum poly_eval_grouped rounds, stays below 2^13 (7636 at most), inside
-// the format; `ok` is cleared otherwise.
+// the format; `ok` is cleared otherwise.  HALF12: c[12] holds half the
+// coefficient of xi_x xi_y, doubled here exactly on the integer pipe.
+template <bool HALF12 = false>
 __device__ __forceinline__ void poly_to_fix(const double (&c)[15], Fix96 (&X)[15], bool& ok) {
   constexpr int E0 = kFixE0 + 39, E1 = kFixE0 + 37, E2 = kFixE0 + 35, E3 = kFixE0 + 33, E4 = kFixE0 + 31;
   X[0] = to_fix_upto<E0>(c[0], ok);
@@ -1011,7 +1078,12 @@ __device__ __forceinline__ void poly_to_fix(const double (&c)[15], Fix96 (&X)[15
   X[9] = to_fix_upto<E1>(c[9], ok);
   X[10] = to_fix_upto<E3>(c[10], ok);
   X[11] = to_fix_upto<E3>(c[11], ok);
-  X[12] = to_fix_upto<E2>(c[12], ok);
+  if constexpr (HALF12) {
+    const Fix96 h = to_fix_upto<E2 - 1>(c[12], ok);
+    X[12] = fix_add(h, h);
+  } else {
+    X[12] = to_fix_upto<E2>(c[12], ok);
+  }
   X[13] = to_fix_upto<E4>(c[13], ok);
   X[14] = to_fix_upto<E4>(c[14], ok);
 }
@@ -1113,15 +1185,16 @@ template <int NT>
 __device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], const LatticeArgs& a,
                                                        double (*s_f)[NT], int tid, double* __restrict__ dst, int x,
                                                        int y) {
-  const Moments mo = site_moments([&](int l) { return f[l]; });
+  const Moments mh = site_moments<-1>([&](int l) { return f[l]; });  // E / 2
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) s_f[l][tid] = f[l];
-  const SiteFields sf = site_fields(mo, a);
+  // the site fields for the caller (unused by the plain step, which drops them)
+  const SiteFields sf = site_fields(Moments{mh.rho, mh.Jx, mh.Jy, mh.Exi + mh.Exi}, a);
   double P[15];
-  eq_monomials(sf, a, P);
+  eq_monomials_moments(mh, a, P);
   bool ok = true;
   Fix96 X[15];
-  poly_to_fix(P, X, ok);
+  poly_to_fix<true>(P, X, ok);
   if (!ok) {  // float64 path for this site
     double g[NPOP];
 #pragma unroll
@@ -1133,7 +1206,7 @@ __device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], 
   }
   double sw[NSHELL];  // omega rho w_j
 #pragma unroll
-  for (int j = 0; j < NSHELL; ++j) sw[j] = sf.rho * a.ow_shell[j];
+  for (int j = 0; j < NSHELL; ++j) sw[j] = mh.rho * a.ow_shell[j];
   dst[sidx(a, 0, y, x)] = fma(a.omc, s_f[0][tid], sw[0] * P[0]);
   poly_eval_grouped(X, [&](int k, Fix96 ev, Fix96 od) {
     const double w = sw[pair_shell(k)];
