@@ -44,21 +44,22 @@ WORKLOAD = "D2Q37 FP64 step, Rayleigh-Taylor 2048x4096, 32 modes, tau=0.6, g=1e-
 # moment sums 110, site fields 9, gravity shift and Hermite coefficients 30,
 # per-shell terms 81, per-pair polynomial and relaxation 312: 542.
 # The kernel forms the moment sums and evaluates the equilibrium polynomial at
-# the 36 moving velocities exactly in fixed point on the integer pipe; the
-# float64 work it keeps is: site fields 9, gravity shift and Hermite
-# coefficients 30, the 15 monomial coefficients of the equilibrium 42, the
-# eight shell factors rho omega w_j 8, one multiply and one FMA per
-# population 111: 200.  ncu counts 145.2 FP64 instructions per site on this
-# kernel (DFMA 65.0, DMUL 74.1, DADD 6.1: 210 flops, the 200 plus the Newton
-# steps of 1/rho).
+# the 36 moving velocities exactly in fixed point on the integer pipe, and
+# takes the equilibrium coefficients straight from the moment sums; the
+# float64 work it keeps is: r^2 / rho, the shifted velocity, its squares and
+# theta 16, the Hermite coefficients 19, the 15 monomial coefficients of the
+# equilibrium 34, the eight shell factors rho omega w_j 8, one multiply and one
+# FMA per population 111: 188.  ncu counts 131.2 FP64 instructions per site on
+# this kernel (DFMA 62.0, DMUL 66.1, DADD 3.1: 193 flops, the 188 plus the
+# Newton-Raphson step of 1/rho).
 FP64_FLOP_PER_SITE = 542
-FP64_PIPE_FLOP_PER_SITE = 200
-FP64_INSTR_PER_SITE_NCU = 145.2
-FP64_PIPE_FLOP_PER_SITE_NCU = 210.2
+FP64_PIPE_FLOP_PER_SITE = 188
+FP64_INSTR_PER_SITE_NCU = 131.2
+FP64_PIPE_FLOP_PER_SITE_NCU = 193.2
 # DRAM bytes per site of the float64 step (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one 2048 x 1024 launch, 1191.80 MB / 2097152 sites;
+# dram__bytes_write.sum of one 2048 x 1024 launch, 1192.06 MB / 2097152 sites;
 # traffic grows with the site count, so a full launch is scaled by sites).
-FP64_TRAFFIC_BYTES_PER_SITE_NCU = 568.30
+FP64_TRAFFIC_BYTES_PER_SITE_NCU = 568.42
 BYTES_PER_SITE_FP64 = 2 * 37 * 8
 BYTES_PER_SITE_FP32 = 2 * 37 * 4
 FP64_NOMINAL_TFLOPS = 1.25
