@@ -95,12 +95,7 @@ __global__ void __launch_bounds__(ABX * ABY, LBM_ADJ_MINB) adjoint_kernel(const 
     for (int l = 0; l < NPOP; ++l) f[l] = dec(l, g[l]);
   }
   walls(src, x, y, a, f, dec, [](int, double v) { return v; });
-  const Moments mo = site_moments([&](int l) { return f[l]; });
-  const SiteFields sf = site_fields(mo, a);
-  const double theta = sf.T + a.tshift;
-  const double uys = sf.uy - a.tau_g_xi;
-  const double v_x = a.r2 * sf.ux, v_y = a.r2 * uys;
-  const double U2 = a.r2 * fma(sf.ux, sf.ux, uys * uys);
+  const AdjSite q = adj_site(site_moments<-1>([&](int l) { return f[l]; }), a);  // from rho, J, E / 2
   // the cotangents wait in shared memory: the fixed-point sums and the
   // relaxation read them twice, and registers hold the accumulators
   __shared__ double s_lam[NPOP][ABX * ABY];
@@ -110,15 +105,17 @@ __global__ void __launch_bounds__(ABX * ABY, LBM_ADJ_MINB) adjoint_kernel(const 
   const auto lam = [&](int l) { return s_lam[l][tid]; };
   double L[15];
   if (!cotangent_moments_fix(lam, a, L)) cotangent_moments(lam, a, L);
-  const EqCot s = eq_cotangent_mono(L, v_x, v_y, U2, theta, a);
-  // gamma_q = sum_m lam_m d f^eq_m / d q for q = rho, Jx, Jy, Exi (xi units)
-  const double usq = fma(sf.ux, sf.ux, sf.uy * sf.uy);
-  const double gJx = a.r2 * fma(-s.Sth, sf.ux, fma(2.0 * a.inv_r2 * v_x, s.SU, s.Scx));
-  const double gJy = a.r2 * fma(-s.Sth, sf.uy, fma(2.0 * a.inv_r2 * v_y, s.SU, s.Scy));
+  const EqCot s = eq_cotangent_site(L, q, a);
+  // gamma_q = sum_m lam_m d f^eq_m / d q for q = rho, Jx, Jy, Exi (xi units),
+  // with r^2 u = (v_x, vy0): G = r^2 (S_cu + 2 S_U v / r^2), gamma_J =
+  // G - S_theta r^2 u, gamma_rho = S_P - u . G + S_theta ((r^2/2) |u|^2 - T)
+  const double SU2 = s.SU + s.SU;
+  const double Gx = fma(q.v_x, SU2, a.r2 * s.Scx), Gy = fma(q.v_y, SU2, a.r2 * s.Scy);
+  const double gJx = fma(-s.Sth, q.v_x, Gx);
+  const double gJy = fma(-s.Sth, q.vy0, Gy);
   const double gE = a.r2_2 * s.Sth;
-  const double gR = s.SP - a.r2 * (sf.ux * (s.Scx + 2.0 * a.inv_r2 * v_x * s.SU) +
-                                   sf.uy * (s.Scy + 2.0 * a.inv_r2 * v_y * s.SU)) +
-                    s.Sth * fma(a.r2_2, usq, -sf.T);
+  const double Q = fma(fma(q.vy0, q.vy0, q.vx2), a.half_inv_r2, a.tshift - q.theta);  // (r^2/2) |u|^2 - T
+  const double gR = fma(s.Sth, Q, fma(-a.inv_r2, fma(q.v_x, Gx, q.vy0 * Gy), s.SP));
   const double wR = a.omega * gR, wJx = a.omega * gJx, wJy = a.omega * gJy, wE = a.omega * gE;
   // mu_l = (1 - omega) lam_l + omega (gR + gJ . xi_l + gE |xi_l|^2)
   double mu[NPOP];

@@ -165,60 +165,88 @@ __device__ __forceinline__ bool cotangent_moments_fix(GetLam lam, const LatticeA
   return true;
 }
 
+// Site quantities of the float64 adjoint, straight from the moment sums
+// (rho, J and E / 2) as in the forward step's coefficients: with
+// s = r^2 / rho, v = (J_x s, J_y s - r^2 tau g / r) is the shifted velocity
+// (r^2 u' in the lattice's units), vy0 = r^2 u_y the unshifted one,
+// U2 = |v|^2 / r^2, theta = T + tshift, h = 1/2 - U2/4 (h2 = 2 h exactly),
+// and the theta multiples t2 = theta r^2 / 2 = B11 r^2 = 2 B21 r^2 and
+// t4 = theta r^2 / 4 = B21 r^2.
+struct AdjSite {
+  double v_x, v_y, vy0, vx2, vy2, vxy, v2, U2, theta, h, h2, t2, t4;
+};
+
+__device__ __forceinline__ AdjSite adj_site(const Moments& mh, const LatticeArgs& a) {
+  AdjSite q;
+  const double s = a.r2 * rcp_nr(mh.rho);
+  q.v_x = mh.Jx * s;
+  q.vy0 = mh.Jy * s;
+  q.v_y = q.vy0 - a.r2_tau_g_xi;
+  q.vx2 = q.v_x * q.v_x;
+  q.vy2 = q.v_y * q.v_y;
+  q.vxy = q.v_x * q.v_y;
+  q.v2 = q.vx2 + q.vy2;
+  q.U2 = q.v2 * a.inv_r2;
+  q.theta = fma(mh.Exi, s, fma(-0.5, q.U2, fma(-a.tau_g_xi, q.v_y, a.tshift_v)));
+  q.h = fma(-0.25, q.U2, 0.5);
+  q.h2 = fma(-0.5, q.U2, 1.0);
+  q.t2 = q.theta * a.r2_2;
+  q.t4 = q.theta * a.r2_4;
+  return q;
+}
+
 // The cotangent sums of eq_cotangent in monomial form: with the w-weighted
 // cotangent moments L_i = sum_l w_l lam_l xi_l^(c_i, e_i), every sum is a
-// contraction of Lam with the monomial coefficients of the polynomial it sums
+// contraction of L with the monomial coefficients of the polynomial it sums
 // (P, dP/dU2, dP/dtheta, and P_cu times xi_x or xi_y, whose monomials are
-// those of P_cu shifted by one degree in x or y).
-__device__ __forceinline__ EqCot eq_cotangent_mono(const double (&L)[15], double v_x, double v_y, double U2,
-                                                   double theta, const LatticeArgs& a) {
-  const EqCoef B = eq_coef(U2, theta);
-  const double r2 = a.r2, r4 = r2 * r2;
-  const double vx2 = v_x * v_x, vy2 = v_y * v_y, vxy = v_x * v_y;
-  const double B01r2 = B.B01 * r2, B02r4 = B.B02 * r4, B21r2 = B.B21 * r2, B11r2 = B.B11 * r2;
-  const double vx2_6 = vx2 * (1.0 / 6.0), vy2_6 = vy2 * (1.0 / 6.0);
-  // The monomial coefficients of the four polynomials (P, dP/dU2, dP/dtheta
-  // and P_cu expanded from cu = xi . v and c2 = r^2 |xi|^2), written out so
-  // that their zero coefficients cost nothing.
+// those of P_cu shifted by one degree in x or y).  The Hermite coefficients
+// are folded as in the forward step (B10 = 2 (h - theta), B01 r^2 = t2 B10,
+// B02 r^4 = t2 t4); the coefficients of P_cu xi of degree 3 equal those of
+// P (C7 = P30, C8 = P12, C10 = P03, C11 = P21, because 2 B21 r^2 = B11 r^2).
+__device__ __forceinline__ EqCot eq_cotangent_site(const double (&L)[15], const AdjSite& q, const LatticeArgs& a) {
+  const double theta = q.theta, U2 = q.U2, v_x = q.v_x, v_y = q.v_y;
+  const double vx2 = q.vx2, vy2 = q.vy2, vxy = q.vxy, t2 = q.t2, t4 = q.t4;
+  const double B20 = fma(-1.5, theta, q.h);
+  const double B10 = fma(-2.0, theta, q.h2);
+  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(q.h2, q.h, 0.5));
+  const double B01r2 = t2 * B10, q8 = t2 * t4;  // B01 r^2, B02 r^4
+  const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);
+  const double Hx = fma(0.5, vx2, t2), Hy = fma(0.5, vy2, t2);
+  // monomial coefficients of P (P30 P12 P03 P21 double as C7 C8 C10 C11)
+  const double P30 = v_x * I, P12 = v_x * Hy, P03 = v_y * J, P21 = v_y * Hx;
+  const double B20x2 = B20 + B20;
   EqCot s;
   {  // P = A0 + A1 cu + A2 cu^2 + cu^3 / 6 + cu^4 / 24
-    const double P1 = fma(B.B20, vx2, B01r2), P2 = fma(B.B20, vy2, B01r2);
-    const double P3 = fma(B21r2, vx2, fma(vx2 * vx2, 1.0 / 24.0, B02r4));
-    const double P4 = fma(B21r2, vx2 + vy2, fma(0.25 * vx2, vy2, 2.0 * B02r4));
-    const double P5 = fma(B21r2, vy2, fma(vy2 * vy2, 1.0 / 24.0, B02r4));
-    const double P7 = v_x * (B11r2 + vx2_6), P8 = v_x * fma(0.5, vy2, B11r2);
-    const double P10 = v_y * (B11r2 + vy2_6), P11 = v_y * fma(0.5, vx2, B11r2);
-    const double B21r2x2 = 2.0 * B21r2;
-    const double P13 = vxy * (B21r2x2 + vx2_6), P14 = vxy * (B21r2x2 + vy2_6);
-    s.SP = fma(B.B00, L[0], fma(P1, L[1], fma(P2, L[2], fma(P3, L[3], fma(P4, L[4], P5 * L[5])))));
-    s.SP = fma(B.B10, fma(v_x, L[6], v_y * L[9]), s.SP);
-    s.SP = fma(P7, L[7], fma(P8, L[8], fma(P10, L[10], fma(P11, L[11], s.SP))));
-    s.SP = fma(2.0 * B.B20 * vxy, L[12], fma(P13, L[13], fma(P14, L[14], s.SP)));
+    const double P20 = fma(B20, vx2, B01r2), P02 = fma(B20, vy2, B01r2);
+    const double P40 = fma(vx2, fma(vx2, 1.0 / 24.0, t4), q8);
+    const double P22 = fma(t4, q.v2, fma(0.25 * vxy, vxy, q8 + q8));
+    const double P04 = fma(vy2, fma(vy2, 1.0 / 24.0, t4), q8);
+    s.SP = fma(B00, L[0], fma(P20, L[1], fma(P02, L[2], fma(P40, L[3], fma(P22, L[4], P04 * L[5])))));
+    s.SP = fma(B10, fma(v_x, L[6], v_y * L[9]), s.SP);
+    s.SP = fma(P30, L[7], fma(P12, L[8], fma(P03, L[10], fma(P21, L[11], s.SP))));
+    s.SP = fma(B20x2 * vxy, L[12], fma(vxy * I, L[13], fma(vxy * J, L[14], s.SP)));
   }
   {  // dP/dU2 = (U2 / 4 + theta - 1/2) - (theta / 4) c2 - cu / 2 - cu^2 / 4
-    const double a1r2 = -0.25 * theta * r2;
-    s.SU = fma(fma(0.25, U2, theta - 0.5), L[0], fma(fma(-0.25, vx2, a1r2), L[1], fma(-0.25, vy2, a1r2) * L[2]));
+    s.SU = fma(theta - q.h, L[0], fma(fma(-0.25, vx2, -t4), L[1], fma(-0.25, vy2, -t4) * L[2]));
     s.SU = fma(-0.5, fma(v_x, L[6], fma(v_y, L[9], vxy * L[12])), s.SU);
   }
   {  // dP/dtheta = (2 theta + U2 - 1) + (1/2 - 2 theta - U2/4) c2 + (theta / 4) c2^2
      //             + (c2 / 2 - 2) cu + (c2 / 4 - 3/2) cu^2
-    const double a1r2 = fma(-2.0, theta, fma(-0.25, U2, 0.5)) * r2, a2r4 = 0.25 * theta * r4;
-    const double r2q = 0.25 * r2, r2h = 0.5 * r2;
-    s.Sth = fma(fma(2.0, theta, U2 - 1.0), L[0], fma(fma(-1.5, vx2, a1r2), L[1], fma(-1.5, vy2, a1r2) * L[2]));
-    s.Sth = fma(fma(r2q, vx2, a2r4), L[3], fma(fma(r2q, vx2 + vy2, 2.0 * a2r4), L[4], fma(fma(r2q, vy2, a2r4), L[5], s.Sth)));
+     // (2 theta + U2 - 1 = U2 / 2 - B10, 1/2 - 2 theta - U2/4 = B10 - h)
+    const double a1r2 = (B10 - q.h) * a.r2, a2r4 = theta * a.r4_4;
+    s.Sth = fma(fma(0.5, U2, -B10), L[0], fma(fma(-1.5, vx2, a1r2), L[1], fma(-1.5, vy2, a1r2) * L[2]));
+    s.Sth = fma(fma(a.r2_4, vx2, a2r4), L[3],
+                fma(fma(a.r2_4, q.v2, a2r4 + a2r4), L[4], fma(fma(a.r2_4, vy2, a2r4), L[5], s.Sth)));
     s.Sth = fma(-2.0, fma(v_x, L[6], v_y * L[9]), s.Sth);
-    s.Sth = fma(r2h, fma(v_x, L[7] + L[8], fma(v_y, L[10] + L[11], vxy * (L[13] + L[14]))), fma(-3.0 * vxy, L[12], s.Sth));
+    s.Sth = fma(a.r2_2, fma(v_x, L[7] + L[8], fma(v_y, L[10] + L[11], vxy * (L[13] + L[14]))),
+                fma(-3.0 * vxy, L[12], s.Sth));
   }
   {  // P_cu = A1 + 2 A2 cu + cu^2 / 2 + cu^3 / 6, times xi_x or xi_y
-    const double C1 = fma(0.5, vx2, B11r2), C2 = fma(0.5, vy2, B11r2);
-    const double B20x2 = 2.0 * B.B20, B21r2x2 = 2.0 * B21r2;
     const double C6 = B20x2 * v_x, C9 = B20x2 * v_y;
-    const double C7 = v_x * (B21r2x2 + vx2_6), C8 = v_x * fma(0.5, vy2, B21r2x2);
-    const double C10 = v_y * (B21r2x2 + vy2_6), C11 = v_y * fma(0.5, vx2, B21r2x2);
-    s.Scx = fma(B.B10, L[6], fma(C1, L[7], fma(C2, L[8], fma(vxy, L[11], fma(C6, L[1], fma(C9, L[12],
-            fma(C7, L[3], fma(C10, L[14], fma(C11, L[13], C8 * L[4])))))))));
-    s.Scy = fma(B.B10, L[9], fma(C1, L[11], fma(C2, L[10], fma(vxy, L[8], fma(C6, L[12], fma(C9, L[2],
-            fma(C7, L[13], fma(C10, L[5], fma(C11, L[4], C8 * L[14])))))))));
+    s.Scx = fma(B10, L[6], fma(Hx, L[7], fma(Hy, L[8], fma(vxy, L[11], fma(C6, L[1], fma(C9, L[12],
+            fma(P30, L[3], fma(P03, L[14], fma(P21, L[13], P12 * L[4])))))))));
+    s.Scy = fma(B10, L[9], fma(Hx, L[11], fma(Hy, L[10], fma(vxy, L[8], fma(C6, L[12], fma(C9, L[2],
+            fma(P30, L[13], fma(P03, L[5], fma(P21, L[4], P12 * L[14])))))))));
   }
   return s;
 }

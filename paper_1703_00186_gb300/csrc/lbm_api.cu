@@ -154,6 +154,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->tshift = p.tau * (1.0 - p.tau) * p.g * p.g / 2.0 - 1.0;
   a->r2_tau_g_xi = a->r2 * a->tau_g_xi;
   a->tshift_v = a->tshift - a->r2_2 * a->tau_g_xi * a->tau_g_xi;
+  a->half_inv_r2 = 0.5 * a->inv_r2;
   a->rho0 = p.rho0;
   for (int j = 0; j < NSHELL; ++j) {
     a->w_shell[j] = q->w_shell[j];

@@ -135,6 +135,7 @@ struct LatticeArgs {
   double r2_2, r2_4, r4_4, r4_8;  // r^2 / 2, r^2 / 4, r^4 / 4, r^4 / 8
   double r2_tau_g_xi;  // r^2 tau_g_xi
   double tshift_v;     // tshift - (r^2 / 2) tau_g_xi^2
+  double half_inv_r2;  // 1 / (2 r^2)
 };
 
 enum { FP32_ARITH_SPLIT = 0, FP32_ARITH_F64_TERMS = 1, FP32_ARITH_F64_COLLIDE = 2 };
