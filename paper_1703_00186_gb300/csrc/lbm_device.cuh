@@ -754,46 +754,6 @@ __device__ __forceinline__ void reg_moments_f64(const double (&f)[NPOP], double 
   N[12] = N11; N[13] = N31; N[14] = N13;
 }
 
-// Coefficients P of the equilibrium polynomial (4th-order Hermite, with the
-// gravity shift) in the integer-velocity monomials of degree <= 4:
-// f^eq_l = w_l rho P(xi_l), P(xi) = sum_i P_i xi_x^(c_i) xi_y^(e_i), in the
-// order of N (expanded from cu = xi . v and c2 = r^2 |xi|^2).
-__device__ __forceinline__ void eq_monomials(const SiteFields& sf, const LatticeArgs& a, double (&P)[15]) {
-  const double theta = sf.T + a.tshift;
-  const double uys = sf.uy - a.tau_g_xi;
-  const double vx_ = a.r2 * sf.ux, vy_ = a.r2 * uys;
-  const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
-  const double v2 = vx2 + vy2;
-  const double U2 = v2 * a.inv_r2;  // |u|^2 r^2
-  // the Hermite coefficients of eq_coef that enter without a theta multiple
-  // (B11 r^2 = theta r^2 / 2, B21 r^2 = theta r^2 / 4 and B02 r^4 = theta^2
-  // r^4 / 8 use the lattice's multiples of r^2 and r^4)
-  const double h = fma(-0.25, U2, 0.5), h2 = fma(-0.5, U2, 1.0);  // h2 = 2 h exactly
-  const double B20 = fma(-1.5, theta, h);
-  const double B10 = fma(-2.0, theta, h2);  // = 2 (h - theta), rounded once
-  // 1 - U2 / 2 + U2^2 / 8 = 2 h^2 + 1/2
-  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(h2, h, 0.5));
-  const double th2 = theta * theta;
-  const double t4 = theta * a.r2_4, t2 = theta * a.r2_2;
-  const double B01r2 = t2 * B10;  // theta r^2 (h - theta)
-  const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);  // B11 r^2 + v^2 / 6
-  P[0] = B00;
-  P[1] = fma(B20, vx2, B01r2);
-  P[2] = fma(B20, vy2, B01r2);
-  P[3] = fma(th2, a.r4_8, vx2 * fma(vx2, 1.0 / 24.0, t4));
-  P[4] = fma(th2, a.r4_4, fma(t4, v2, 0.25 * (vx2 * vy2)));
-  P[5] = fma(th2, a.r4_8, vy2 * fma(vy2, 1.0 / 24.0, t4));
-  P[6] = B10 * vx_;
-  P[7] = vx_ * I;
-  P[8] = vx_ * fma(0.5, vy2, t2);
-  P[9] = B10 * vy_;
-  P[10] = vy_ * J;
-  P[11] = vy_ * fma(0.5, vx2, t2);
-  P[12] = (B20 + B20) * vxy;
-  P[13] = vxy * I;
-  P[14] = vxy * J;
-}
-
 // 1 / x by one third-order Newton-Raphson correction of a float32 seed
 // (float64 FP-pipe work: three FMAs).  The seed y0 comes from x's top 23
 // significand bits (integer operations), the approximate float32 reciprocal
@@ -815,9 +775,12 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return (ex >= -125 && ex < 126) ? y : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-// eq_monomials for the float64 BGK step, straight from the moment sums
-// (rho, J and E / 2) with the site fields folded in, and with P[12] halved
-// (poly_to_fix<true> doubles it).  With s = r^2 / rho the shifted velocity is
+// Coefficients P of the equilibrium polynomial (4th-order Hermite, with the
+// gravity shift) in the integer-velocity monomials of degree <= 4:
+// f^eq_l = w_l rho P(xi_l), P(xi) = sum_i P_i xi_x^(c_i) xi_y^(e_i), in the
+// order of N (expanded from cu = xi . v and c2 = r^2 |xi|^2), straight from
+// the moment sums (rho, J and E / 2) with the site fields folded in, and with
+// P[12] halved (poly_to_fix<true> doubles it).  With s = r^2 / rho the shifted velocity is
 // v = (J_x s, J_y s - r^2 tau g / r) = r^2 (u - (0, tau g / r)), and
 //   theta = T + tshift,  T = (r^2 / 2) (E / rho - |u|^2),
 //   (r^2 / 2) |u|^2 = U2 / 2 + (tau g / r) v_y + (r^2 / 2) (tau g / r)^2,
@@ -862,15 +825,10 @@ __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const La
   const double N00 = N[0], N20 = N[1], N02 = N[2], N40 = N[3], N22 = N[4], N04 = N[5];
   const double N10 = N[6], N30 = N[7], N12 = N[8], N01 = N[9], N03 = N[10], N21 = N[11];
   const double N11 = N[12], N31 = N[13], N13 = N[14];
-  // site fields (rho, J, E are monomial moments)
-  Moments mo;
-  mo.rho = N00;
-  mo.Jx = N10;
-  mo.Jy = N01;
-  mo.Exi = N20 + N02;
-  const SiteFields sf = site_fields(mo, a);
+  // the equilibrium's coefficients from rho, J and E / 2 (monomial moments);
+  // Pm[12] holds half the xy coefficient
   double Pm[15];
-  eq_monomials(sf, a, Pm);
+  eq_monomials_moments(Moments{N00, N10, N01, 0.5 * (N20 + N02)}, a, Pm);
   const double P00 = Pm[0], P20 = Pm[1], P02 = Pm[2], P40 = Pm[3], P22 = Pm[4], P04 = Pm[5];
   const double P10 = Pm[6], P30 = Pm[7], P12 = Pm[8], P01 = Pm[9], P03 = Pm[10], P21 = Pm[11];
   const double P11 = Pm[12], P31 = Pm[13], P13 = Pm[14];
@@ -895,12 +853,12 @@ __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const La
   blk3(45, N01, N03, N21, qeo);
   blk3(54, N11, N31, N13, qoo);
   // R = omega rho P + (1 - omega) q
-  const double wr = a.omega * sf.rho;
+  const double wr = a.omega * N00;
   const double R00 = fma(wr, P00, q[0]), R20 = fma(wr, P20, q[1]), R02 = fma(wr, P02, q[2]);
   const double R40 = fma(wr, P40, q[3]), R22 = fma(wr, P22, q[4]), R04 = fma(wr, P04, q[5]);
   const double R10 = fma(wr, P10, qoe[0]), R30 = fma(wr, P30, qoe[1]), R12 = fma(wr, P12, qoe[2]);
   const double R01 = fma(wr, P01, qeo[0]), R03 = fma(wr, P03, qeo[1]), R21 = fma(wr, P21, qeo[2]);
-  const double R11 = fma(wr, P11, qoo[0]), R31 = fma(wr, P31, qoo[1]), R13 = fma(wr, P13, qoo[2]);
+  const double R11 = fma(wr + wr, P11, qoo[0]), R31 = fma(wr, P31, qoo[1]), R13 = fma(wr, P13, qoo[2]);
   Rv[0] = R00; Rv[1] = R20; Rv[2] = R02; Rv[3] = R40; Rv[4] = R22; Rv[5] = R04;
   Rv[6] = R10; Rv[7] = R30; Rv[8] = R12; Rv[9] = R01; Rv[10] = R03; Rv[11] = R21;
   Rv[12] = R11; Rv[13] = R31; Rv[14] = R13;
