@@ -90,6 +90,7 @@ SIGNATURES = {
     "lbm_constants": (c_int, [c_void_p, P(c_double), P(c_double), P(c_double), P(c_double)]),
     "lbm_model_constants": (c_int, [P(LbmParams), P(c_double), P(c_double), P(c_double), P(c_double)]),
     "lbm_probe_fma": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
+    "lbm_probe_rcp": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong]),
     "lbm_batch_tile_count": (c_int, []),
     "lbm_batch_tile_per_lattice": (c_int, [c_int]),
     "lbm_batch_tile_kind": (c_int, [c_int]),

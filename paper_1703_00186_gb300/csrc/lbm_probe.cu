@@ -1,8 +1,9 @@
-// FMA throughput probe (include/lbm_probe.h).
+// FMA throughput probe and the site reciprocal (include/lbm_probe.h).
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
 #include "../../include/lbm_probe.h"
+#include "lbm_device.cuh"
 
 namespace {
 
@@ -23,7 +24,21 @@ __global__ void fma_probe_kernel(T* out, int iters, T b, T c) {
   if (s == (T)12345.678) out[0] = s;  // keeps the chains alive; practically never taken
 }
 
+__global__ void rcp_probe_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = lbm::rcp_nr(x[i]);
+}
+
 }  // namespace
+
+extern "C" int lbm_probe_rcp(void* stream, const double* x, double* y, long long n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return LBM_ERR_INVALID;
+  if (n == 0) return LBM_OK;
+  const long long blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffffLL) return LBM_ERR_INVALID;
+  rcp_probe_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
 
 extern "C" int lbm_probe_fma(void* stream, int iters, int fp32, double* tflops, double* ms) {
   if (iters < 1 || !tflops || !ms) return LBM_ERR_INVALID;
