@@ -780,8 +780,9 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // f^eq_l = w_l rho P(xi_l), P(xi) = sum_i P_i xi_x^(c_i) xi_y^(e_i), in the
 // order of N (expanded from cu = xi . v and c2 = r^2 |xi|^2), straight from
 // the moment sums (rho, J and E / 2) with the site fields folded in, and with
-// P[12] halved (poly_to_fix<true> doubles it).  With s = r^2 / rho the shifted velocity is
-// v = (J_x s, J_y s - r^2 tau g / r) = r^2 (u - (0, tau g / r)), and
+// P[12] halved (poly_to_fix<true> doubles it).  With s = r^2 / rho the
+// shifted velocity is v = (J_x s, J_y s - r^2 tau g / r) = r^2 (u - (0,
+// tau g / r)), and
 //   theta = T + tshift,  T = (r^2 / 2) (E / rho - |u|^2),
 //   (r^2 / 2) |u|^2 = U2 / 2 + (tau g / r) v_y + (r^2 / 2) (tau g / r)^2,
 // so theta = (E / 2) s - U2 / 2 - (tau g / r) v_y + tshift_v, where the
@@ -797,9 +798,10 @@ __device__ __forceinline__ void eq_monomials_moments(const Moments& mh, const La
   const double h = fma(-0.25, U2, 0.5), h2 = fma(-0.5, U2, 1.0);  // h2 = 2 h exactly
   const double B20 = fma(-1.5, theta, h);
   const double B10 = fma(-2.0, theta, h2);  // = 2 (h - theta), rounded once
+  // 1 - U2 / 2 + U2^2 / 8 = 2 h^2 + 1/2
   const double B00 = fma(theta, (U2 - 1.0) + theta, fma(h2, h, 0.5));
   const double t4 = theta * a.r2_4, t2 = theta * a.r2_2;
-  const double B01r2 = t2 * B10;
+  const double B01r2 = t2 * B10;  // theta r^2 (h - theta)
   const double q8 = t2 * t4, q4 = t2 * t2;
   const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);
   P[0] = B00;
