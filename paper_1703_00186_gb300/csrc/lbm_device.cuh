@@ -424,6 +424,13 @@ __device__ __forceinline__ SiteFields collide_fp64(double (&f)[NPOP], const Latt
 // rho |u|^2 / 2, rho u_y, with the mid-step hydrodynamic velocity (physical
 // units) u_h = (u_x, u_y + g / 2) of the stored post-collide state.
 constexpr int NOBS = 8;
+
+// The fields site_observables takes: rho, the physical u_x, the physical u_y
+// minus g / 2 and T.
+struct ObsFields {
+  double rho, ux, uy, T;
+};
+
 __device__ __forceinline__ void site_observables(double rho, double ux, double uy_h, double T, double (&o)[NOBS]) {
   o[0] = rho;
   o[1] = ux;
@@ -788,7 +795,11 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // so theta = (E / 2) s - U2 / 2 - (tau g / r) v_y + tshift_v, where the
 // lattice constant tshift_v = tshift - (r^2 / 2) (tau g / r)^2.  Products
 // of the theta multiples: theta^2 r^4 / 8 = t2 t4 and theta^2 r^4 / 4 = t2^2.
-__device__ __forceinline__ void eq_monomials_moments(const Moments& mh, const LatticeArgs& a, double (&P)[15]) {
+struct EqSite {
+  double vx, vy, theta;  // r^2 u_x, r^2 (u_y - tau g / r), T + tshift
+};
+
+__device__ __forceinline__ EqSite eq_monomials_moments(const Moments& mh, const LatticeArgs& a, double (&P)[15]) {
   const double s = a.r2 * rcp_nr(mh.rho);
   const double vx_ = mh.Jx * s, vy_ = fma(mh.Jy, s, -a.r2_tau_g_xi);
   const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
@@ -819,6 +830,7 @@ __device__ __forceinline__ void eq_monomials_moments(const Moments& mh, const La
   P[12] = B20 * vxy;  // half
   P[13] = vxy * I;
   P[14] = vxy * J;
+  return EqSite{vx_, vy_, theta};
 }
 
 // The regularised collide's coefficients R of the new populations
@@ -1142,16 +1154,14 @@ __device__ __forceinline__ void collide_fp64_reg_grouped(const double (&f_in)[NP
 // shared memory (s_f[l][tid]) for the relaxation.  Sites with a coefficient
 // outside poly_to_fix's range take collide_fp64.
 template <int NT>
-__device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], const LatticeArgs& a,
-                                                       double (*s_f)[NT], int tid, double* __restrict__ dst, int x,
-                                                       int y) {
+__device__ __forceinline__ ObsFields collide_fp64_fix(const double (&f)[NPOP], const LatticeArgs& a,
+                                                      double (*s_f)[NT], int tid, double* __restrict__ dst, int x,
+                                                      int y) {
   const Moments mh = site_moments<-1>([&](int l) { return f[l]; });  // E / 2
 #pragma unroll
   for (int l = 0; l < NPOP; ++l) s_f[l][tid] = f[l];
-  // the site fields for the caller (unused by the plain step, which drops them)
-  const SiteFields sf = site_fields(Moments{mh.rho, mh.Jx, mh.Jy, mh.Exi + mh.Exi}, a);
   double P[15];
-  eq_monomials_moments(mh, a, P);
+  const EqSite q = eq_monomials_moments(mh, a, P);
   bool ok = true;
   Fix96 X[15];
   poly_to_fix<true>(P, X, ok);
@@ -1159,10 +1169,10 @@ __device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], 
     double g[NPOP];
 #pragma unroll
     for (int l = 0; l < NPOP; ++l) g[l] = s_f[l][tid];
-    collide_fp64(g, a);
+    const SiteFields sf = collide_fp64(g, a);
 #pragma unroll
     for (int l = 0; l < NPOP; ++l) dst[sidx(a, l, y, x)] = g[l];
-    return sf;
+    return ObsFields{sf.rho, a.r * sf.ux, a.r * sf.uy - 0.5 * a.g, sf.T};
   }
   double sw[NSHELL];  // omega rho w_j
 #pragma unroll
@@ -1173,7 +1183,9 @@ __device__ __forceinline__ SiteFields collide_fp64_fix(const double (&f)[NPOP], 
     dst[sidx(a, 2 * k + 1, y, x)] = fma(a.omc, s_f[2 * k + 1][tid], w * fix_to_double(fix_add(ev, od)));
     dst[sidx(a, 2 * k + 2, y, x)] = fma(a.omc, s_f[2 * k + 2][tid], w * fix_to_double(fix_sub(ev, od)));
   });
-  return sf;
+  // the fields for the measurement routines (dropped by the plain step):
+  // r u_x = v_x / r, r u_y - g / 2 = v_y / r + tau g - g / 2, T = theta - tshift
+  return ObsFields{mh.rho, q.vx * a.inv_r, fma(q.vy, a.inv_r, a.uy_obs_shift), q.theta - a.tshift};
 }
 
 // Equilibrium f^eq(rho, u, T) (physical u) into 37 float64 values.

@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(BX * BY, 4) step_observe_kernel(const double* 
     else pull(src, x, y, a, f);
     walls(src, x, y, a, f, codec, [&](int l, double v) { return codec.enc(l, v); });
     __shared__ double s_f[NPOP][BX * BY];
-    const SiteFields sf = collide_fp64_fix<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
-    site_observables(sf.rho, a.r * sf.ux, a.r * sf.uy - 0.5 * a.g, sf.T, o);
+    const ObsFields of = collide_fp64_fix<BX * BY>(f, a, s_f, threadIdx.y * BX + threadIdx.x, dst, x, y);
+    site_observables(of.rho, of.ux, of.uy, of.T, o);
   }
   constexpr unsigned kAll = 0xffffffffu;
   bool ok = true;
