@@ -169,11 +169,12 @@ __device__ __forceinline__ bool cotangent_moments_fix(GetLam lam, const LatticeA
 // (rho, J and E / 2) as in the forward step's coefficients: with
 // s = r^2 / rho, v = (J_x s, J_y s - r^2 tau g / r) is the shifted velocity
 // (r^2 u' in the lattice's units), vy0 = r^2 u_y the unshifted one,
-// U2 = |v|^2 / r^2, theta = T + tshift, h = 1/2 - U2/4 (h2 = 2 h exactly),
+// v2 = |v|^2 (U2 = v2 / r^2 enters only through multiples), theta =
+// T + tshift, h = 1/2 - U2/4 (h2 = 2 h exactly),
 // and the theta multiples t2 = theta r^2 / 2 = B11 r^2 = 2 B21 r^2 and
 // t4 = theta r^2 / 4 = B21 r^2.
 struct AdjSite {
-  double v_x, v_y, vy0, vx2, vy2, vxy, v2, U2, theta, h, h2, t2, t4;
+  double v_x, v_y, vy0, vx2, vy2, vxy, v2, theta, h, h2, t2, t4;
 };
 
 __device__ __forceinline__ AdjSite adj_site(const Moments& mh, const LatticeArgs& a) {
@@ -186,10 +187,9 @@ __device__ __forceinline__ AdjSite adj_site(const Moments& mh, const LatticeArgs
   q.vy2 = q.v_y * q.v_y;
   q.vxy = q.v_x * q.v_y;
   q.v2 = q.vx2 + q.vy2;
-  q.U2 = q.v2 * a.inv_r2;
-  q.theta = fma(mh.Exi, s, fma(-0.5, q.U2, fma(-a.tau_g_xi, q.v_y, a.tshift_v)));
-  q.h = fma(-0.25, q.U2, 0.5);
-  q.h2 = fma(-0.5, q.U2, 1.0);
+  q.theta = fma(mh.Exi, s, fma(-a.half_inv_r2, q.v2, fma(-a.tau_g_xi, q.v_y, a.tshift_v)));
+  q.h = fma(-a.quarter_inv_r2, q.v2, 0.5);
+  q.h2 = fma(-a.half_inv_r2, q.v2, 1.0);
   q.t2 = q.theta * a.r2_2;
   q.t4 = q.theta * a.r2_4;
   return q;
@@ -204,11 +204,11 @@ __device__ __forceinline__ AdjSite adj_site(const Moments& mh, const LatticeArgs
 // B02 r^4 = t2 t4); the coefficients of P_cu xi of degree 3 equal those of
 // P (C7 = P30, C8 = P12, C10 = P03, C11 = P21, because 2 B21 r^2 = B11 r^2).
 __device__ __forceinline__ EqCot eq_cotangent_site(const double (&L)[15], const AdjSite& q, const LatticeArgs& a) {
-  const double theta = q.theta, U2 = q.U2, v_x = q.v_x, v_y = q.v_y;
+  const double theta = q.theta, v_x = q.v_x, v_y = q.v_y;
   const double vx2 = q.vx2, vy2 = q.vy2, vxy = q.vxy, t2 = q.t2, t4 = q.t4;
   const double B20 = fma(-1.5, theta, q.h);
   const double B10 = fma(-2.0, theta, q.h2);
-  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(q.h2, q.h, 0.5));
+  const double B00 = fma(theta, fma(a.inv_r2, q.v2, -1.0) + theta, fma(q.h2, q.h, 0.5));
   const double B01r2 = t2 * B10, q8 = t2 * t4;  // B01 r^2, B02 r^4
   const double I = fma(vx2, 1.0 / 6.0, t2), J = fma(vy2, 1.0 / 6.0, t2);
   const double Hx = fma(0.5, vx2, t2), Hy = fma(0.5, vy2, t2);
@@ -234,7 +234,7 @@ __device__ __forceinline__ EqCot eq_cotangent_site(const double (&L)[15], const 
      //             + (c2 / 2 - 2) cu + (c2 / 4 - 3/2) cu^2
      // (2 theta + U2 - 1 = U2 / 2 - B10, 1/2 - 2 theta - U2/4 = B10 - h)
     const double a1r2 = (B10 - q.h) * a.r2, a2r4 = theta * a.r4_4;
-    s.Sth = fma(fma(0.5, U2, -B10), L[0], fma(fma(-1.5, vx2, a1r2), L[1], fma(-1.5, vy2, a1r2) * L[2]));
+    s.Sth = fma(fma(a.half_inv_r2, q.v2, -B10), L[0], fma(fma(-1.5, vx2, a1r2), L[1], fma(-1.5, vy2, a1r2) * L[2]));
     s.Sth = fma(fma(a.r2_4, vx2, a2r4), L[3],
                 fma(fma(a.r2_4, q.v2, a2r4 + a2r4), L[4], fma(fma(a.r2_4, vy2, a2r4), L[5], s.Sth)));
     s.Sth = fma(-2.0, fma(v_x, L[6], v_y * L[9]), s.Sth);

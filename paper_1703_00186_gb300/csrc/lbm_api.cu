@@ -155,6 +155,7 @@ int make_lattice_args(const lbm_params& p, LatticeArgs* a, char* err, size_t err
   a->r2_tau_g_xi = a->r2 * a->tau_g_xi;
   a->tshift_v = a->tshift - a->r2_2 * a->tau_g_xi * a->tau_g_xi;
   a->half_inv_r2 = 0.5 * a->inv_r2;
+  a->quarter_inv_r2 = 0.25 * a->inv_r2;
   a->inv_r = 1.0 / q->r;
   a->uy_obs_shift = p.tau * p.g - 0.5 * p.g;
   a->rho0 = p.rho0;

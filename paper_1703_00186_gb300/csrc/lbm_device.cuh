@@ -799,18 +799,31 @@ struct EqSite {
   double vx, vy, theta;  // r^2 u_x, r^2 (u_y - tau g / r), T + tshift
 };
 
+// VIA_V2: U2 enters only through multiples of v2 = |v|^2 (one product fewer;
+// measured faster in the regularised collide, 0.3 % slower in the BGK step).
+template <bool VIA_V2 = false>
 __device__ __forceinline__ EqSite eq_monomials_moments(const Moments& mh, const LatticeArgs& a, double (&P)[15]) {
   const double s = a.r2 * rcp_nr(mh.rho);
   const double vx_ = mh.Jx * s, vy_ = fma(mh.Jy, s, -a.r2_tau_g_xi);
   const double vx2 = vx_ * vx_, vy2 = vy_ * vy_, vxy = vx_ * vy_;
   const double v2 = vx2 + vy2;
-  const double U2 = v2 * a.inv_r2;
-  const double theta = fma(mh.Exi, s, fma(-0.5, U2, fma(-a.tau_g_xi, vy_, a.tshift_v)));
-  const double h = fma(-0.25, U2, 0.5), h2 = fma(-0.5, U2, 1.0);  // h2 = 2 h exactly
+  double theta, h, h2, U2m1;  // h2 = 2 h exactly; U2m1 = U2 - 1
+  if constexpr (VIA_V2) {
+    theta = fma(mh.Exi, s, fma(-a.half_inv_r2, v2, fma(-a.tau_g_xi, vy_, a.tshift_v)));
+    h = fma(-a.quarter_inv_r2, v2, 0.5);
+    h2 = fma(-a.half_inv_r2, v2, 1.0);
+    U2m1 = fma(a.inv_r2, v2, -1.0);
+  } else {
+    const double U2 = v2 * a.inv_r2;
+    theta = fma(mh.Exi, s, fma(-0.5, U2, fma(-a.tau_g_xi, vy_, a.tshift_v)));
+    h = fma(-0.25, U2, 0.5);
+    h2 = fma(-0.5, U2, 1.0);
+    U2m1 = U2 - 1.0;
+  }
   const double B20 = fma(-1.5, theta, h);
   const double B10 = fma(-2.0, theta, h2);  // = 2 (h - theta), rounded once
   // 1 - U2 / 2 + U2^2 / 8 = 2 h^2 + 1/2
-  const double B00 = fma(theta, (U2 - 1.0) + theta, fma(h2, h, 0.5));
+  const double B00 = fma(theta, U2m1 + theta, fma(h2, h, 0.5));
   const double t4 = theta * a.r2_4, t2 = theta * a.r2_2;
   const double B01r2 = t2 * B10;  // theta r^2 (h - theta)
   const double q8 = t2 * t4, q4 = t2 * t2;
@@ -842,7 +855,7 @@ __device__ __forceinline__ void reg_coefficients(const double (&N)[15], const La
   // the equilibrium's coefficients from rho, J and E / 2 (monomial moments);
   // Pm[12] holds half the xy coefficient
   double Pm[15];
-  eq_monomials_moments(Moments{N00, N10, N01, 0.5 * (N20 + N02)}, a, Pm);
+  eq_monomials_moments<true>(Moments{N00, N10, N01, 0.5 * (N20 + N02)}, a, Pm);
   const double P00 = Pm[0], P20 = Pm[1], P02 = Pm[2], P40 = Pm[3], P22 = Pm[4], P04 = Pm[5];
   const double P10 = Pm[6], P30 = Pm[7], P12 = Pm[8], P01 = Pm[9], P03 = Pm[10], P21 = Pm[11];
   const double P11 = Pm[12], P31 = Pm[13], P13 = Pm[14];

@@ -136,6 +136,7 @@ struct LatticeArgs {
   double r2_tau_g_xi;  // r^2 tau_g_xi
   double tshift_v;     // tshift - (r^2 / 2) tau_g_xi^2
   double half_inv_r2;  // 1 / (2 r^2)
+  double quarter_inv_r2;  // 1 / (4 r^2)
   double inv_r;         // 1 / r
   double uy_obs_shift;  // tau g - g / 2
 };
